@@ -1,0 +1,659 @@
+/*
+ * lbm13_oracle.c -- plain FP64 CPU oracle of the D2Q13 energy-conserving
+ * multiple-relaxation-time lattice Boltzmann time step of Lallemand & Dubois,
+ * "Comparison of Simulations of Convective Flows" (Commun. Comput. Phys. 2015).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is loaded by tests/, by the smoke check
+ * of the package entry module and by the CPU-baseline leg of bench.py, and by
+ * nothing else.  It shares no code, header, table or constant generator with
+ * the CUDA path: every number below is rebuilt here from the paper.
+ *
+ * What it computes, in the paper's order and notation:
+ *   Sec. 2, Eq. (d2q13-vitesses)   13 velocities v_j (D2Q9 + the four (+-2,0),(0,+-2)).
+ *   Sec. 2, Eq. (d2q13-polynomes)  moment matrix M_kj = p_k(v_j) (k, j = 0..12).
+ *   Sec. 2, Eq. (d2q13-moments-equil) equilibria of the 9 non-conserved moments.
+ *   Sec. 2, Eqs. (d2q13-henon), (d2q13-diffusion), (d2q13-sigma-qx)
+ *                                   derived constants h1, k1, h2, c2, c_erho, sigma_q.
+ *   collision  m* = m - S (m - m_eq),  f* = M^-1 m*   (dense 13x13 products)
+ *   streaming  f_j(x + v_j, t+1) = f*_j(x, t), periodic or through a wall
+ *   Sec. 7, Eq. (d2q13-cl-abb)      mixed bounce-back / anti-bounce-back walls.
+ *   Sec. 5 and Sec. 8               buoyancy and body force.
+ *   Sec. 10, Table 1 and Fig. 14    Nusselt number and centro-asymmetry read-outs.
+ *
+ * Readings where the paper is silent, garbled or inconsistent (each one is a
+ * choice, stated once here and in the design notes):
+ *   R1 q_x = x(-3 + x^2 + y^2), q_y = y(-3 + x^2 + y^2): with the printed +3 the
+ *      basis is not orthogonal (sum_j x_j * x_j (3 + |v_j|^2) = 84).
+ *   R2 the index range of Eq. (d2q13-moments) is 0..12, not 0..8.
+ *   R3 rates: s_qy = s_qx, s_ry = s_rx, s_XY = s_XX.
+ *   R4 sigma_XX = 104 nu / (13 c1 + 95 + 2 E0)  (shear viscosity of the basis).
+ *   R5 Pr is nu over the decay rate of the diffusive (entropy) mode.
+ *   R7 temperature T = p / rho with p = (E + 28 rho)/26 - |j|^2/(2 rho).
+ *   R9 forcing F = (rho - rho_ref) g; equilibria taken at j + F/2; after the
+ *      collision j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2) / rho.
+ *   R10 walls lie half a link outside the first and last node; a population
+ *      that leaves x_f with velocity v and crosses the wall at fraction a of the
+ *      link lands at x_f + (2a - 1) v with velocity -v.
+ *   R11 at a velocity+temperature wall the links normal to the wall use
+ *      anti-bounce-back, the diagonal links bounce-back.
+ *   R12 wall density rho_w = 1.5 rho(first node) - 0.5 rho(second node).
+ *   R13 an adiabatic wall bounces every link back.
+ *   R14 bounce-back off a moving wall adds -2 f^eq,odd_j(wall).
+ *   R15 Nu = (1/(Ny kappa dT)) sum_nodes [u_x (T - Tm) - kappa D_x T], kappa = nu/Pr.
+ *   R16 asymmetry S_u = max |u(i,j) + u(nx-1-i, ny-1-j)|.
+ *   R17 residual r_F = ||F^n - F^{n-K}||_2 / (K max(||F^n - mean F^n||_2, 1e-6 sqrt(N))).
+ *   corners: a diagonal that crosses two walls at once bounces back with the
+ *      mean of the two walls' data.
+ *
+ * Storage: post-collision distributions f*(t), plane-major f[j][y][x], FP64.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 13
+
+/* Sec. 2: velocities, in the paper's index order j = 0..12. */
+static const int vx_of[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1, 2, 0, -2, 0};
+static const int vy_of[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1, 0, 2, 0, -2};
+
+/* moment order k = 0..12: rho, E, eps, varpi, jx, jy, qx, qy, rx, ry, XX, XY, XXe */
+enum { K_RHO, K_E, K_EPS, K_VPI, K_JX, K_JY, K_QX, K_QY, K_RX, K_RY, K_XX, K_XY, K_XXE };
+
+typedef struct {
+    double E0, c1, k2, c_epsE, c_vpi_rho, c_vpi_E, Pr, nu, s_eps, s_vpi, s_r, s_XXe;
+} orc_params;
+
+typedef struct { int kind; double u_t; double T; } orc_wall; /* 0 periodic, 1 adiabatic BB, 2 mixed */
+typedef struct {
+    orc_wall west, east, south, north;
+    double gx, gy, rho_ref;
+} orc_boundary;
+
+typedef struct {
+    int nx, ny, nthreads;
+    orc_params p;
+    orc_boundary b;
+    /* basis */
+    double M[Q][Q], D[Q], Minv[Q][Q];
+    /* derived constants (Sec. 2) */
+    double A, B, h1, k1, h2, c2, c_erho, sigma_XX, sigma_q, s[Q];
+    /* state: post-collision f*(t) and a scratch for streaming */
+    double *f, *g;
+    long t;
+    /* residual snapshot of (ux, uy, T) and the step at which it was taken */
+    double *snap;
+    long snap_t;
+    int have_snap;
+} orc_lattice;
+
+/* ---------------------------------------------------------------- basis */
+
+/* Eq. (d2q13-polynomes), evaluated at (x, y) = v_j; R1 for q. */
+static double poly(int k, double x, double y)
+{
+    double r2 = x * x + y * y;
+    switch (k) {
+    case K_RHO: return 1.0;
+    case K_E:   return -28.0 + 13.0 * r2;
+    case K_EPS: return 140.0 + r2 * (-361.0 / 2.0 + 77.0 * r2 / 2.0);
+    case K_VPI: return -12.0 + r2 * (581.0 / 12.0 + r2 * (-273.0 / 8.0 + 137.0 / 24.0 * r2));
+    case K_JX:  return x;
+    case K_JY:  return y;
+    case K_QX:  return x * (-3.0 + r2);
+    case K_QY:  return y * (-3.0 + r2);
+    case K_RX:  return x * (101.0 / 6.0 + r2 * (-63.0 / 4.0 + 35.0 / 12.0 * r2));
+    case K_RY:  return y * (101.0 / 6.0 + r2 * (-63.0 / 4.0 + 35.0 / 12.0 * r2));
+    case K_XX:  return x * x - y * y;
+    case K_XY:  return x * y;
+    default:    return (x * x - y * y) * (-65.0 / 12.0 + 17.0 / 12.0 * r2);
+    }
+}
+
+/* Variant with the printed sign of q (used only by the erratum test). */
+static double poly_printed_q(int k, double x, double y)
+{
+    double r2 = x * x + y * y;
+    if (k == K_QX) return x * (3.0 + r2);
+    if (k == K_QY) return y * (3.0 + r2);
+    return poly(k, x, y);
+}
+
+/* M_kj = p_k(v_j) (Eq. d2q13-moments, R2), D_k = sum_j M_kj^2.  The moments
+ * are orthogonal (Sec. 2), so M^-1 = M^T D^-1: (M^-1)_jk = M_kj / D_k. */
+void orc_basis(double *M_out, double *D_out, double *Minv_out, int printed_q_sign)
+{
+    double M[Q][Q], Minv[Q][Q];
+    for (int k = 0; k < Q; ++k)
+        for (int j = 0; j < Q; ++j) {
+            double v = printed_q_sign ? poly_printed_q(k, vx_of[j], vy_of[j]) : poly(k, vx_of[j], vy_of[j]);
+            /* the polynomials take integer values on this stencil; the
+             * fractions of Eq. (d2q13-polynomes) leave rounding noise of a few
+             * ulp, removed here (a non-integer value is kept as it is) */
+            double r = nearbyint(v);
+            M[k][j] = fabs(v - r) < 1e-9 ? r : v;
+        }
+    for (int k = 0; k < Q; ++k) {
+        double d = 0.0;
+        for (int j = 0; j < Q; ++j) d += M[k][j] * M[k][j];
+        if (D_out) D_out[k] = d;
+    }
+    if (M_out) memcpy(M_out, M, sizeof M);
+    if (Minv_out) {
+        for (int j = 0; j < Q; ++j)
+            for (int k = 0; k < Q; ++k) {
+                double d = 0.0;
+                for (int i = 0; i < Q; ++i) d += M[k][i] * M[k][i];
+                Minv[j][k] = M[k][j] / d;
+            }
+        memcpy(Minv_out, Minv, sizeof Minv);
+    }
+}
+
+void orc_velocities(int *vx, int *vy)
+{
+    for (int j = 0; j < Q; ++j) { vx[j] = vx_of[j]; vy[j] = vy_of[j]; }
+}
+
+/* ------------------------------------------------------ derived constants */
+
+/* Eqs. (d2q13-henon), (d2q13-diffusion), (d2q13-sigma-qx) and R4.
+ * Returns 0, or -1 when a rate leaves (0, 2). */
+static int derive(orc_lattice *L)
+{
+    const orc_params *p = &L->p;
+    double E0 = p->E0, c1 = p->c1, k2 = p->k2, ceE = p->c_epsE;
+    L->A = 13.0 * c1 + 95.0 + 2.0 * E0;
+    L->B = 114404.0 + 51051.0 * c1 - 11492.0 * ceE + 7854.0 * E0;
+    L->h1 = 17.0 / 26.0 - c1 / 2.0 - E0 / 13.0;
+    L->k1 = 2.0 / 13.0;
+    L->h2 = -(39.0 / 2.0 + 13.0 / 2.0 * c1 + E0) * k2
+            - 7.0 / 624.0 * L->A * (874481.0 + 459459.0 * c1 - 103428.0 * ceE + 70686.0 * E0) / L->B;
+    L->sigma_XX = 104.0 * p->nu / L->A;
+    L->sigma_q = -1309.0 / 2.0 * L->sigma_XX * L->A / L->B;
+    L->c_erho = 140.0 + 28.0 * ceE + L->A * L->B / (22984.0 * p->Pr);
+    L->c2 = -65.0 / 24.0 - 21.0 / 8.0 * (c1 + L->h1 + L->k1 * E0) - k2 * E0 - L->h2;
+    double sXX = 1.0 / (L->sigma_XX + 0.5), sq = 1.0 / (L->sigma_q + 0.5);
+    for (int k = 0; k < Q; ++k) L->s[k] = 0.0;     /* conserved: rho, E, jx, jy */
+    L->s[K_EPS] = p->s_eps;
+    L->s[K_VPI] = p->s_vpi;
+    L->s[K_QX] = L->s[K_QY] = sq;                  /* R3 */
+    L->s[K_RX] = L->s[K_RY] = p->s_r;
+    L->s[K_XX] = L->s[K_XY] = sXX;
+    L->s[K_XXE] = p->s_XXe;
+    int nc[9] = {K_EPS, K_VPI, K_QX, K_QY, K_RX, K_RY, K_XX, K_XY, K_XXE};
+    for (int i = 0; i < 9; ++i)
+        if (!(L->s[nc[i]] > 0.0 && L->s[nc[i]] < 2.0)) return -1;
+    if (!(L->A > 0.0)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------ equilibria */
+
+/* Eq. (d2q13-moments-equil): the equilibrium moment vector for the conserved
+ * values (rho, E, jx, jy); the conserved entries are the values themselves. */
+static void equilibrium_moments(const orc_lattice *L, double rho, double E, double jx, double jy, double meq[Q])
+{
+    const orc_params *p = &L->p;
+    meq[K_RHO] = rho;
+    meq[K_E] = E;
+    meq[K_JX] = jx;
+    meq[K_JY] = jy;
+    meq[K_EPS] = L->c_erho * rho + p->c_epsE * E;
+    meq[K_VPI] = p->c_vpi_rho * rho + p->c_vpi_E * E;
+    meq[K_QX] = jx * (p->c1 + L->h1 * rho + L->k1 * E);
+    meq[K_QY] = jy * (p->c1 + L->h1 * rho + L->k1 * E);
+    meq[K_RX] = jx * (L->c2 + L->h2 * rho + p->k2 * E);
+    meq[K_RY] = jy * (L->c2 + L->h2 * rho + p->k2 * E);
+    meq[K_XX] = (jx * jx - jy * jy) / rho;
+    meq[K_XY] = jx * jy / rho;
+    meq[K_XXE] = 0.0;
+}
+
+static void to_distribution(const orc_lattice *L, const double m[Q], double f[Q])
+{
+    for (int j = 0; j < Q; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += L->Minv[j][k] * m[k];
+        f[j] = s;
+    }
+}
+
+static void to_moments(const orc_lattice *L, const double f[Q], double m[Q])
+{
+    for (int k = 0; k < Q; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < Q; ++j) s += L->M[k][j] * f[j];
+        m[k] = s;
+    }
+}
+
+/* ------------------------------------------------------------- collision */
+
+/* One node: m = M f; equilibria at j + F/2 (R9); relax the nine
+ * non-conserved moments; update the conserved ones by the force; f* = M^-1 m*. */
+static void collide(const orc_lattice *L, const double f[Q], double fs[Q])
+{
+    double m[Q], meq[Q], ms[Q];
+    to_moments(L, f, m);
+    double rho = m[K_RHO], E = m[K_E], jx = m[K_JX], jy = m[K_JY];
+    double Fx = (rho - L->b.rho_ref) * L->b.gx, Fy = (rho - L->b.rho_ref) * L->b.gy;
+    equilibrium_moments(L, rho, E, jx + 0.5 * Fx, jy + 0.5 * Fy, meq);
+    for (int k = 0; k < Q; ++k) ms[k] = m[k] - L->s[k] * (m[k] - meq[k]);
+    ms[K_RHO] = rho;
+    ms[K_JX] = jx + Fx;
+    ms[K_JY] = jy + Fy;
+    ms[K_E] = E + 13.0 * ((jx + Fx) * (jx + Fx) + (jy + Fy) * (jy + Fy) - jx * jx - jy * jy) / rho;
+    to_distribution(L, ms, fs);
+}
+
+void orc_collide_node(const orc_lattice *L, const double *f, double *fs) { collide(L, f, fs); }
+
+/* ----------------------------------------------------------------- walls */
+
+typedef struct { double rho, E, ux, uy; } wall_state;
+
+static const orc_wall *wall_of(const orc_lattice *L, int side) /* 0 W, 1 E, 2 S, 3 N */
+{
+    return side == 0 ? &L->b.west : side == 1 ? &L->b.east : side == 2 ? &L->b.south : &L->b.north;
+}
+
+static double node_moment(const orc_lattice *L, const double *fs, int k, int x, int y)
+{
+    size_t plane = (size_t)L->nx * L->ny, at = (size_t)y * L->nx + x;
+    double s = 0.0;
+    for (int j = 0; j < Q; ++j) s += L->M[k][j] * fs[j * plane + at];
+    return s;
+}
+
+/* Wall data at position pos along a side (R12, and R7 for the energy):
+ * rho_w by linear extrapolation of the first two fluid nodes; for a
+ * velocity+temperature wall E_w = rho_w (26 T_w - 28) + 13 rho_w |u_w|^2,
+ * for an adiabatic wall E_w is extrapolated like rho_w. */
+static wall_state wall_data(const orc_lattice *L, const double *fs, int side, int pos)
+{
+    const orc_wall *w = wall_of(L, side);
+    int x0, y0, x1, y1;
+    if (side == 0)      { x0 = 0;          x1 = 1;          y0 = y1 = pos; }
+    else if (side == 1) { x0 = L->nx - 1;  x1 = L->nx - 2;  y0 = y1 = pos; }
+    else if (side == 2) { y0 = 0;          y1 = 1;          x0 = x1 = pos; }
+    else                { y0 = L->ny - 1;  y1 = L->ny - 2;  x0 = x1 = pos; }
+    wall_state s;
+    double r0 = node_moment(L, fs, K_RHO, x0, y0), r1 = node_moment(L, fs, K_RHO, x1, y1);
+    s.rho = 1.5 * r0 - 0.5 * r1;
+    if (side <= 1) { s.ux = 0.0; s.uy = w->u_t; } else { s.ux = w->u_t; s.uy = 0.0; }
+    if (w->kind == 2) {
+        s.E = s.rho * (26.0 * w->T - 28.0) + 13.0 * s.rho * (s.ux * s.ux + s.uy * s.uy);
+    } else {
+        double e0 = node_moment(L, fs, K_E, x0, y0), e1 = node_moment(L, fs, K_E, x1, y1);
+        s.E = 1.5 * e0 - 0.5 * e1;
+    }
+    return s;
+}
+
+/* Even or odd part (under v -> -v) of the equilibrium distribution in
+ * direction j at the wall state: sum over the even or odd moments of
+ * M_kj m_eq,k / D_k. */
+static double feq_part(const orc_lattice *L, const wall_state *w, int j, int odd)
+{
+    double meq[Q];
+    equilibrium_moments(L, w->rho, w->E, w->rho * w->ux, w->rho * w->uy, meq);
+    static const int is_odd[Q] = {0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 0, 0};
+    double s = 0.0;
+    for (int k = 0; k < Q; ++k)
+        if (is_odd[k] == odd) s += L->M[k][j] * meq[k] / L->D[k];
+    return s;
+}
+
+static int opposite(int j)
+{
+    for (int i = 0; i < Q; ++i)
+        if (vx_of[i] == -vx_of[j] && vy_of[i] == -vy_of[j]) return i;
+    return -1;
+}
+
+/* ------------------------------------------------------------- streaming */
+
+/* Push every post-collision population f*_j(x_f) along v_j.  Inside the
+ * domain (after periodic wrapping) it lands at x_f + v_j.  A population that
+ * crosses a wall follows R10-R14.  Every destination slot is written exactly
+ * once; the scratch is filled with NaN first so that a slot nobody writes is
+ * detected (returns -1). */
+static int stream(orc_lattice *L)
+{
+    const int nx = L->nx, ny = L->ny;
+    const size_t plane = (size_t)nx * ny;
+    const double *fs = L->f;
+    double *g = L->g;
+    int input_has_nan = 0;
+    for (size_t i = 0; i < Q * plane; ++i) {
+        if (isnan(fs[i])) input_has_nan = 1;
+        g[i] = NAN;
+    }
+    const int per_x = L->b.west.kind == 0, per_y = L->b.south.kind == 0;
+
+#pragma omp parallel for schedule(static) num_threads(L->nthreads)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            for (int j = 0; j < Q; ++j) {
+                double val = fs[j * plane + (size_t)y * nx + x];
+                int tx = x + vx_of[j], ty = y + vy_of[j];
+                if (per_x) tx = ((tx % nx) + nx) % nx;
+                if (per_y) ty = ((ty % ny) + ny) % ny;
+                int out_x = tx < 0 || tx >= nx, out_y = ty < 0 || ty >= ny;
+                if (!out_x && !out_y) {
+                    g[j * plane + (size_t)ty * nx + tx] = val;
+                    continue;
+                }
+                int jb = opposite(j);
+                if (out_x && out_y) {
+                    /* corner diagonal: lands on x_f, bounce-back with the mean
+                     * of the two walls' data */
+                    int sx = tx < 0 ? 0 : 1, sy = ty < 0 ? 2 : 3;
+                    wall_state a = wall_data(L, fs, sx, y), b = wall_data(L, fs, sy, x), c;
+                    c.rho = 0.5 * (a.rho + b.rho);
+                    c.E = 0.5 * (a.E + b.E);
+                    c.ux = 0.5 * (a.ux + b.ux);
+                    c.uy = 0.5 * (a.uy + b.uy);
+                    g[jb * plane + (size_t)y * nx + x] = val - 2.0 * feq_part(L, &c, j, 1);
+                    continue;
+                }
+                /* one wall: side, coordinate along it, and the landing node
+                 * x_f + (2a - 1) v with a the fraction of the link inside */
+                int side, pos, lx = x, ly = y;
+                int normal_link;
+                if (out_x) {
+                    side = tx < 0 ? 0 : 1;
+                    pos = y;
+                    double wall = side == 0 ? -0.5 : nx - 0.5;
+                    double a = (wall - x) / vx_of[j];
+                    lx = (int)lround(x + (2.0 * a - 1.0) * vx_of[j]);
+                    ly = (int)lround(y + (2.0 * a - 1.0) * vy_of[j]);
+                    normal_link = vy_of[j] == 0;
+                } else {
+                    side = ty < 0 ? 2 : 3;
+                    pos = x;
+                    double wall = side == 2 ? -0.5 : ny - 0.5;
+                    double a = (wall - y) / vy_of[j];
+                    lx = (int)lround(x + (2.0 * a - 1.0) * vx_of[j]);
+                    ly = (int)lround(y + (2.0 * a - 1.0) * vy_of[j]);
+                    normal_link = vx_of[j] == 0;
+                }
+                const orc_wall *w = wall_of(L, side);
+                wall_state ws = wall_data(L, fs, side, pos);
+                double out;
+                if (w->kind == 2 && normal_link)
+                    out = -val + 2.0 * feq_part(L, &ws, j, 0);   /* anti-bounce-back, R11 */
+                else
+                    out = val - 2.0 * feq_part(L, &ws, j, 1);    /* bounce-back, R13/R14 */
+                g[jb * plane + (size_t)ly * nx + lx] = out;
+            }
+        }
+    }
+    if (!input_has_nan)
+        for (size_t i = 0; i < Q * plane; ++i)
+            if (isnan(g[i])) return -1;
+    return 0;
+}
+
+/* --------------------------------------------------------------- lattice */
+
+orc_lattice *orc_create(int nx, int ny, const orc_params *p, const orc_boundary *b, int nthreads)
+{
+    if (nx < 2 || ny < 2) return NULL;
+    if ((b->west.kind == 0) != (b->east.kind == 0)) return NULL;
+    if ((b->south.kind == 0) != (b->north.kind == 0)) return NULL;
+    if (b->west.kind != 0 && nx < 4) return NULL;
+    if (b->south.kind != 0 && ny < 4) return NULL;
+    orc_lattice *L = (orc_lattice *)calloc(1, sizeof *L);
+    if (!L) return NULL;
+    L->nx = nx;
+    L->ny = ny;
+    L->nthreads = nthreads > 0 ? nthreads : 1;
+    L->p = *p;
+    L->b = *b;
+    orc_basis(&L->M[0][0], L->D, &L->Minv[0][0], 0);
+    if (derive(L) != 0) { free(L); return NULL; }
+    size_t n = (size_t)Q * nx * ny;
+    L->f = (double *)malloc(n * sizeof(double));
+    L->g = (double *)malloc(n * sizeof(double));
+    L->snap = (double *)malloc((size_t)3 * nx * ny * sizeof(double));
+    if (!L->f || !L->g || !L->snap) { free(L->f); free(L->g); free(L->snap); free(L); return NULL; }
+    return L;
+}
+
+void orc_destroy(orc_lattice *L)
+{
+    if (!L) return;
+    free(L->f);
+    free(L->g);
+    free(L->snap);
+    free(L);
+}
+
+/* Derived constants, for the pins: A, B, h1, k1, h2, c2, c_erho, sigma_XX,
+ * sigma_q, then the 13 rates s_k, then the 13 rest weights w_j = f_eq at
+ * (rho, E, j) = (1, E0, 0), then T0. */
+void orc_constants(const orc_lattice *L, double *out)
+{
+    out[0] = L->A; out[1] = L->B; out[2] = L->h1; out[3] = L->k1; out[4] = L->h2;
+    out[5] = L->c2; out[6] = L->c_erho; out[7] = L->sigma_XX; out[8] = L->sigma_q;
+    for (int k = 0; k < Q; ++k) out[9 + k] = L->s[k];
+    double meq[Q], w[Q];
+    equilibrium_moments(L, 1.0, L->p.E0, 0.0, 0.0, meq);
+    to_distribution(L, meq, w);
+    for (int j = 0; j < Q; ++j) out[22 + j] = w[j];
+    out[35] = (L->p.E0 + 28.0) / 26.0;
+}
+
+/* Initial state: f*(0) = f_eq(rho, j = rho u, E) with E from the temperature
+ * through R7: E = rho (26 T - 28) + 13 rho |u|^2.  Arrays are [ny][nx]. */
+void orc_set_equilibrium(orc_lattice *L, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    const size_t plane = (size_t)L->nx * L->ny;
+    for (size_t i = 0; i < plane; ++i) {
+        double r = rho[i], u = ux[i], v = uy[i];
+        double E = r * (26.0 * T[i] - 28.0) + 13.0 * r * (u * u + v * v);
+        double meq[Q], feq[Q];
+        equilibrium_moments(L, r, E, r * u, r * v, meq);
+        to_distribution(L, meq, feq);
+        for (int j = 0; j < Q; ++j) L->f[j * plane + i] = feq[j];
+    }
+    L->t = 0;
+    L->have_snap = 0;
+}
+
+void orc_set_raw(orc_lattice *L, const double *f)
+{
+    memcpy(L->f, f, sizeof(double) * Q * (size_t)L->nx * L->ny);
+    L->t = 0;
+    L->have_snap = 0;
+}
+
+void orc_get_raw(const orc_lattice *L, double *f)
+{
+    memcpy(f, L->f, sizeof(double) * Q * (size_t)L->nx * L->ny);
+}
+
+/* n time steps: stream the stored f*(t), then collide every node. */
+int orc_step(orc_lattice *L, long n)
+{
+    const size_t plane = (size_t)L->nx * L->ny;
+    for (long it = 0; it < n; ++it) {
+        if (stream(L) != 0) return -1;
+#pragma omp parallel for schedule(static) num_threads(L->nthreads)
+        for (long i = 0; i < (long)plane; ++i) {
+            double f[Q], fs[Q];
+            for (int j = 0; j < Q; ++j) f[j] = L->g[j * plane + i];
+            collide(L, f, fs);
+            for (int j = 0; j < Q; ++j) L->f[j * plane + i] = fs[j];
+        }
+        L->t += 1;
+    }
+    return 0;
+}
+
+long orc_time(const orc_lattice *L) { return L->t; }
+
+/* The 13 moments of the stored state, [k][ny][nx]. */
+void orc_moments(const orc_lattice *L, double *out)
+{
+    const size_t plane = (size_t)L->nx * L->ny;
+    for (size_t i = 0; i < plane; ++i) {
+        double f[Q], m[Q];
+        for (int j = 0; j < Q; ++j) f[j] = L->f[j * plane + i];
+        to_moments(L, f, m);
+        for (int k = 0; k < Q; ++k) out[k * plane + i] = m[k];
+    }
+}
+
+/* Macroscopic fields of the stored post-collision state, [4][ny][nx]:
+ * rho; u = (j* - F/2)/rho (the momentum half-way through the force step);
+ * T = p/rho with p = (E* + 28 rho)/26 - |j*|^2/(2 rho) (R7; the force step
+ * changes E by exactly the kinetic energy, so p is the same before and after). */
+void orc_macro(const orc_lattice *L, double *out)
+{
+    const size_t plane = (size_t)L->nx * L->ny;
+    for (size_t i = 0; i < plane; ++i) {
+        double f[Q], m[Q];
+        for (int j = 0; j < Q; ++j) f[j] = L->f[j * plane + i];
+        to_moments(L, f, m);
+        double rho = m[K_RHO];
+        double Fx = (rho - L->b.rho_ref) * L->b.gx, Fy = (rho - L->b.rho_ref) * L->b.gy;
+        double p = (m[K_E] + 28.0 * rho) / 26.0 - (m[K_JX] * m[K_JX] + m[K_JY] * m[K_JY]) / (2.0 * rho);
+        out[0 * plane + i] = rho;
+        out[1 * plane + i] = (m[K_JX] - 0.5 * Fx) / rho;
+        out[2 * plane + i] = (m[K_JY] - 0.5 * Fy) / rho;
+        out[3 * plane + i] = p / rho;
+    }
+}
+
+/* Compensated (Kahan) sum helper. */
+typedef struct { double s, c; } ksum;
+static void kadd(ksum *k, double v)
+{
+    double y = v - k->c, t = k->s + y;
+    k->c = (t - k->s) - y;
+    k->s = t;
+}
+
+/* Read-outs, out[16]:
+ *  0 residual max_F r_F (R17), 1..3 r_ux, r_uy, r_T (0 on the first call),
+ *  4..7 totals of rho, jx, jy, E of the stored state (Kahan sums),
+ *  8 Nu (R15; 0 unless west and east are temperature walls with T_w != T_e),
+ *  9 S_u, 10 S_T (R16, S_T on T - Tm), 11 max |u|, 12 count of non-finite
+ *  values in the state, 13 K (steps since the previous call), 14 t,
+ *  15 mean T.  The call stores (ux, uy, T) as the next snapshot. */
+void orc_residual(orc_lattice *L, double *out)
+{
+    const int nx = L->nx, ny = L->ny;
+    const size_t plane = (size_t)nx * ny;
+    double *mac = (double *)malloc(4 * plane * sizeof(double));
+    double *mom = (double *)malloc(Q * plane * sizeof(double));
+    orc_macro(L, mac);
+    orc_moments(L, mom);
+    const double *rho = mac, *ux = mac + plane, *uy = mac + 2 * plane, *T = mac + 3 * plane;
+    for (int i = 0; i < 16; ++i) out[i] = 0.0;
+
+    ksum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int kk[4] = {K_RHO, K_JX, K_JY, K_E};
+    for (int a = 0; a < 4; ++a)
+        for (size_t i = 0; i < plane; ++i) kadd(&tot[a], mom[kk[a] * plane + i]);
+    for (int a = 0; a < 4; ++a) out[4 + a] = tot[a].s;
+
+    double nonfinite = 0.0;
+    for (size_t i = 0; i < Q * plane; ++i)
+        if (!isfinite(L->f[i])) nonfinite += 1.0;
+    out[12] = nonfinite;
+
+    /* residual against the snapshot */
+    long K = L->t - L->snap_t;
+    if (L->have_snap && K > 0) {
+        const double *F[3] = {ux, uy, T};
+        double rmax = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double mean = 0.0;
+            for (size_t i = 0; i < plane; ++i) mean += F[a][i];
+            mean /= (double)plane;
+            double num = 0.0, den = 0.0;
+            for (size_t i = 0; i < plane; ++i) {
+                double d = F[a][i] - L->snap[a * plane + i];
+                num += d * d;
+                double e = F[a][i] - mean;
+                den += e * e;
+            }
+            num = sqrt(num);
+            den = sqrt(den);
+            /* a field whose RMS variation is below 1e-6 counts as flat at that scale */
+            double floor_ = 1e-6 * sqrt((double)plane);
+            double r = num / ((double)K * (den > floor_ ? den : floor_));
+            out[1 + a] = r;
+            if (r > rmax) rmax = r;
+        }
+        out[0] = rmax;
+    }
+    out[13] = (double)(L->have_snap ? K : 0);
+    out[14] = (double)L->t;
+
+    /* Nusselt number (R15) */
+    double Tm = 0.0;
+    for (size_t i = 0; i < plane; ++i) Tm += T[i];
+    Tm /= (double)plane;
+    out[15] = Tm;
+    if (L->b.west.kind == 2 && L->b.east.kind == 2 && L->b.west.T != L->b.east.T && nx >= 3) {
+        double dT = L->b.west.T - L->b.east.T, Tref = 0.5 * (L->b.west.T + L->b.east.T);
+        double kappa = L->p.nu / L->p.Pr;
+        double sum = 0.0;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t i = (size_t)y * nx + x;
+                double dTdx;
+                if (x == 0)
+                    dTdx = (-3.0 * T[i] + 4.0 * T[i + 1] - T[i + 2]) / 2.0;
+                else if (x == nx - 1)
+                    dTdx = (3.0 * T[i] - 4.0 * T[i - 1] + T[i - 2]) / 2.0;
+                else
+                    dTdx = (T[i + 1] - T[i - 1]) / 2.0;
+                sum += ux[i] * (T[i] - Tref) - kappa * dTdx;
+            }
+        out[8] = sum / ((double)ny * kappa * dT);
+    }
+
+    /* centro-asymmetry (R16) and max |u| */
+    double Tref = Tm;
+    if (L->b.west.kind == 2 && L->b.east.kind == 2) Tref = 0.5 * (L->b.west.T + L->b.east.T);
+    double Su = 0.0, ST = 0.0, umax = 0.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t i = (size_t)y * nx + x, m = (size_t)(ny - 1 - y) * nx + (nx - 1 - x);
+            double sx = ux[i] + ux[m], sy = uy[i] + uy[m];
+            double su = sqrt(sx * sx + sy * sy);
+            double st = fabs((T[i] - Tref) + (T[m] - Tref));
+            double um = sqrt(ux[i] * ux[i] + uy[i] * uy[i]);
+            if (su > Su) Su = su;
+            if (st > ST) ST = st;
+            if (um > umax) umax = um;
+        }
+    out[9] = Su;
+    out[10] = ST;
+    out[11] = umax;
+    (void)rho;
+
+    memcpy(L->snap, mac + plane, 3 * plane * sizeof(double));
+    L->snap_t = L->t;
+    L->have_snap = 1;
+    free(mac);
+    free(mom);
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,165 @@
+"""Pins of the oracle's full time step against closed forms: transverse-wave
+decay at the viscosity the rates imply (config of Sec. 6), Couette and
+Poiseuille profiles with the mixed walls of Sec. 7 and the body force of
+Sec. 8, pure conduction between temperature walls, exact mass and energy
+conservation in an adiabatic box (Sec. 9), and the read-outs of Sec. 10."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+NU = 0.05
+
+
+def _T0(p):
+    return (p["E0"] + 28) / 26
+
+
+def test_shear_wave_decays_at_nu_k2(pstar):
+    """64 x 64 periodic, u_x = 0.01 sin(2 pi y / 64): amplitude ~ exp(-nu k^2 t)."""
+    n = 64
+    lat = O.Lattice(n, n, pstar)
+    y = np.arange(n)[:, None] * np.ones((1, n))
+    s = np.sin(2 * np.pi * y / n)
+    lat.set_equilibrium(1.0, 0.01 * s, 0.0, _T0(pstar))
+    amp = lambda: 2 * np.mean(lat.macro()[1] * s)
+    lat.step(200)
+    a1 = amp()
+    lat.step(800)
+    a2 = amp()
+    k = 2 * np.pi / n
+    assert np.log(a2 / a1) / 800 == pytest.approx(-NU * k * k, rel=1e-4)
+
+
+def test_poiseuille_profile_converges_at_second_order(pstar):
+    """BB walls at rest, body force g: u = g eta (H - eta) / (2 nu), eta = y + 1/2
+    (walls half a link outside the first and last node, reading R10)."""
+    errs = []
+    for H in (8, 16):
+        b = O.boundary(south=O.wall(O.WALL_BB), north=O.wall(O.WALL_BB), gx=1e-6, rho_ref=0.0)
+        lat = O.Lattice(4, H, pstar, b)
+        lat.set_equilibrium(1.0, 0.0, 0.0, _T0(pstar))
+        lat.step(int(3 * H * H / NU))
+        u = lat.macro()[1][:, 0]
+        eta = np.arange(H) + 0.5
+        exact = 1e-6 * eta * (H - eta) / (2 * NU)
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    assert errs[1] < 5e-3
+    assert errs[0] / errs[1] > 3.5
+
+
+def test_couette_profile_is_linear(pstar):
+    """Velocity+temperature walls (Sec. 7): lower wall at rest, upper wall moving
+    at U, both at T0: u = U (y + 1/2) / H.  The anti-bounce-back links are not
+    mass-tight (the wall density is extrapolated, reading R12), so a wall-normal
+    velocity of order 1e-5 U remains; the temperature moves by less than 1e-3 U
+    (a parabolic deficit of about 0.8 times the Brinkman heating, opposite sign)."""
+    H, U = 16, 0.01
+    T0 = _T0(pstar)
+    b = O.boundary(south=O.wall(O.WALL_MIXED, 0.0, T0), north=O.wall(O.WALL_MIXED, U, T0))
+    lat = O.Lattice(4, H, pstar, b)
+    lat.set_equilibrium(1.0, 0.0, 0.0, T0)
+    lat.step(int(3 * H * H / NU))
+    rho, ux, uy, T = lat.macro()
+    eta = np.arange(H) + 0.5
+    exact = U * eta / H
+    assert np.linalg.norm(ux[:, 0] - exact) / np.linalg.norm(exact) < 5e-4
+    assert np.abs(uy).max() < 1e-4 * U
+    assert np.abs(T - T0).max() < 1e-3 * U
+
+
+def test_conduction_profile_is_linear(pstar):
+    """Temperature walls at T0 +- dT/2, no flow: T linear in x (anti-bounce-back
+    imposes the wall temperature, Eq. d2q13-cl-abb) and Nu = 1."""
+    W, dT = 16, 1e-4
+    T0 = _T0(pstar)
+    b = O.boundary(west=O.wall(O.WALL_MIXED, 0.0, T0 + dT / 2), east=O.wall(O.WALL_MIXED, 0.0, T0 - dT / 2))
+    lat = O.Lattice(W, 4, pstar, b)
+    lat.set_equilibrium(1.0, 0.0, 0.0, T0)
+    lat.step(int(4 * W * W * pstar["Pr"] / NU))
+    T = lat.macro()[3]
+    x = np.arange(W) + 0.5
+    exact = T0 + dT / 2 - dT * x / W
+    assert np.abs(T - exact[None, :]).max() < 1e-4 * dT
+    r = lat.residual()
+    assert r[8] == pytest.approx(1.0, abs=1e-6)
+
+
+def test_adiabatic_box_conserves_mass_and_energy(pstar):
+    """All four walls bounce back (R13): nothing crosses them, so the totals of
+    rho and E stay fixed to round-off while the state relaxes."""
+    b = O.boundary(west=O.wall(O.WALL_BB), east=O.wall(O.WALL_BB), south=O.wall(O.WALL_BB), north=O.wall(O.WALL_BB))
+    lat = O.Lattice(12, 10, pstar, b)
+    w = lat.constants()["w"]
+    rng = np.random.default_rng(20260101)
+    lat.set_raw(w[:, None, None] * (1 + 1e-2 * rng.standard_normal((13, 10, 12))))
+    m0 = lat.moments().sum(axis=(1, 2))
+    f0 = lat.get_raw()
+    lat.step(300)
+    m1 = lat.moments().sum(axis=(1, 2))
+    assert abs(m1[0] - m0[0]) < 1e-13 * 120
+    assert abs(m1[1] - m0[1]) < 1e-13 * 120 * 30
+    assert np.abs(lat.get_raw() - f0).max() > 1e-4
+
+
+def test_periodic_momentum_budget_under_force(pstar):
+    """Periodic lattice, buoyancy F = (rho - 1) g: sum j grows by sum F per step."""
+    n = 16
+    g = -1e-4
+    b = O.boundary(gy=g, rho_ref=1.0)
+    lat = O.Lattice(n, n, pstar, b)
+    rng = np.random.default_rng(7)
+    w = lat.constants()["w"]
+    lat.set_raw(w[:, None, None] * (1 + 1e-3 * rng.standard_normal((13, n, n))))
+    m0 = lat.moments()
+    lat.step(50)
+    m1 = lat.moments()
+    sF = ((m0[0] - 1.0) * g).sum()
+    # round-off of 256 nodes x 50 steps of dense 13 x 13 transforms: ~1e-12
+    assert m1[0].sum() == pytest.approx(m0[0].sum(), abs=1e-11)
+    assert m1[5].sum() - m0[5].sum() == pytest.approx(50 * sF, rel=1e-7)
+    assert abs(m1[4].sum() - m0[4].sum()) < 1e-11
+
+
+def test_asymmetry_readout(pstar):
+    """Fig. 14's measure max |V(x) + V(x0 - x)| is 0 for a centro-symmetric
+    field and 2c for a uniform flow c."""
+    n = 8
+    T0 = _T0(pstar)
+    b = O.boundary(west=O.wall(O.WALL_MIXED, 0.0, T0 + 0.01), east=O.wall(O.WALL_MIXED, 0.0, T0 - 0.01),
+                   south=O.wall(O.WALL_BB), north=O.wall(O.WALL_BB))
+    lat = O.Lattice(n, n, pstar, b)
+    rng = np.random.default_rng(3)
+    ux = rng.standard_normal((n, n)) * 1e-3
+    ux = ux - ux[::-1, ::-1]
+    uy = rng.standard_normal((n, n)) * 1e-3
+    uy = uy - uy[::-1, ::-1]
+    dT = rng.standard_normal((n, n)) * 1e-3
+    dT = dT - dT[::-1, ::-1]
+    lat.set_equilibrium(1.0, ux, uy, T0 + dT)
+    r = lat.residual()
+    assert r[9] < 1e-15 and r[10] < 1e-15
+    assert r[11] == pytest.approx(np.hypot(ux, uy).max(), rel=1e-12)
+    lat.set_equilibrium(1.0, 0.002, 0.0, T0)
+    assert lat.residual()[9] == pytest.approx(0.004, rel=1e-12)
+
+
+def test_residual_is_zero_at_rest_and_decreases_for_decaying_wave(pstar):
+    n = 32
+    lat = O.Lattice(n, n, pstar)
+    lat.set_equilibrium(1.0, 0.0, 0.0, _T0(pstar))
+    lat.residual()
+    lat.step(10)
+    r = lat.residual()
+    assert r[0] < 1e-9 and r[13] == 10
+    y = np.arange(n)[:, None] * np.ones((1, n))
+    lat.set_equilibrium(1.0, 0.01 * np.sin(2 * np.pi * y / n), 0.0, _T0(pstar))
+    lat.residual()
+    seq = []
+    for _ in range(4):
+        lat.step(100)
+        seq.append(lat.residual()[1])
+    assert all(a > 0 for a in seq)
+    # a pure decay exp(-nu k^2 t): relative change per step ~ nu k^2
+    k = 2 * np.pi / n
+    assert seq[-1] == pytest.approx((np.exp(NU * k * k * 100) - 1) / 100, rel=2e-3)
