@@ -1,0 +1,339 @@
+"""Throughput of the fused D2Q13 time step on GB300.
+
+Workload (one bench step = one time step of the whole lattice): the periodic
+transverse shear wave u_x = 0.01 sin(2 pi y / n) of the throughput sweep, at
+n x n = 8192 x 8192 by default, parameters nu = 0.05, Pr = 0.71, in
+FP32-deviation storage (104 algorithmic bytes per lattice update).  The FP64
+path (208 B/LU) is measured on the same lattice and reported beside it.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline per GB300; p50/p99 time-to-steady-state vs plain FP64"
+UNIT = "MLUPS"
+NU, PR = 0.05, 0.71
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=60)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def traffic_record(tag):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 3 and parts[0] == tag and parts[1] == digest:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(steps_target_s=12.0, n=512):
+    """The FP64 oracle as it stands, on the host cores: n x n shear wave."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1401_0188_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    p = O.pstar(NU, PR)
+    lat = O.Lattice(n, n, p, nthreads=cores)
+    ux, uy = W.shear_wave(n, n, 0.01)
+    lat.set_equilibrium(1.0, ux, uy, (p["E0"] + 28) / 26)
+    t = time.perf_counter()
+    lat.step(2)
+    per = (time.perf_counter() - t) / 2
+    steps = max(2, int(steps_target_s / max(per, 1e-6)))
+    t = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": n * n * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n}x{n} periodic shear wave, {steps} steps, FP64 oracle, {cores} OpenMP threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import build as ob, oracle as O
+    from paper_1401_0188_gb300 import workloads as W
+    ob.build()
+    n = 512
+    cores = os.cpu_count() or 1
+    p = O.pstar(NU, PR)
+    lat = O.Lattice(n, n, p, nthreads=cores)
+    ux, uy = W.shear_wave(n, n, 0.01)
+    lat.set_equilibrium(1.0, ux, uy, (p["E0"] + 28) / 26)
+    lat.step(args.warmup)
+    t = time.perf_counter()
+    lat.step(args.steps)
+    dt = time.perf_counter() - t
+    v = n * n * args.steps / dt / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"periodic shear wave u_x=0.01 sin(2 pi y/n), bounded sample {n}x{n} of the "
+                                  f"{args.size}x{args.size} lattice (MLUPS is per node)", "nu": NU, "Pr": PR,
+                      "precision": "fp64", "l2": "n/a (CPU)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n}x{n}, {args.steps} timed steps after {args.warmup}"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def time_steps(lat, steps, torch):
+    stream = lat.stream
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    lat.step(steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    return start.elapsed_time(end)  # ms
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1401_0188_gb300 import build as lb
+    if rank == 0 or world == 1:
+        lb.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1401_0188_gb300 import lbm13, pstar, rest_temperature, workloads as W
+
+    n = args.size
+    p = pstar(NU, PR)
+    T0 = rest_temperature(p)
+    prec = lbm13.FP32_DEVIATION if args.precision == "fp32" else lbm13.FP64
+    elem = 4 if prec == lbm13.FP32_DEVIATION else 8
+    bytes_lu = 26 * elem
+    dev = torch.device("cuda", local)
+
+    def device_fields():
+        y = torch.arange(n, device=dev, dtype=torch.float64)[:, None].expand(n, n)
+        ux = (0.01 * torch.sin(2 * torch.pi * y / n)).contiguous()
+        return (torch.ones(n, n, device=dev, dtype=torch.float64), ux,
+                torch.zeros(n, n, device=dev, dtype=torch.float64),
+                torch.full((n, n), T0, device=dev, dtype=torch.float64))
+
+    lat = lbm13.Lattice(n, n, p, W.boundary(), precision=prec)
+    f = device_fields()
+    lat.set_state_device(*f)
+    del f
+    lat.step(args.warmup)
+    lat.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as clk:
+        ms = time_steps(lat, args.steps, torch)
+    elapsed = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.all_reduce(elapsed, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(elapsed.item())
+    per_launch_s = ms / 1e3 / args.steps
+    value = world * n * n * args.steps / (ms_max / 1e3) / 1e6
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_lu * n * n / per_launch_s / 1e9
+    tag = f"step_{args.precision}_{n}"
+    traffic = traffic_record(tag)
+
+    # end to end through the C ABI with host buffers: upload fields, step, read back
+    e2e = None
+    if not args.no_e2e:
+        y = torch.arange(n, dtype=torch.float64)[:, None].expand(n, n)
+        host = [torch.ones(n, n, dtype=torch.float64).pin_memory(),
+                (0.01 * torch.sin(2 * torch.pi * y / n)).contiguous().pin_memory(),
+                torch.zeros(n, n, dtype=torch.float64).pin_memory(),
+                torch.full((n, n), T0, dtype=torch.float64).pin_memory()]
+        out = torch.empty(4, n, n, dtype=torch.float64).pin_memory()
+        mask = 1 | lbm13.FIELD_UX | lbm13.FIELD_UY | lbm13.FIELD_T
+        import ctypes
+        dp = ctypes.POINTER(ctypes.c_double)
+        ptrs = [ctypes.cast(h.data_ptr(), dp) for h in host]
+        outp = ctypes.cast(out.data_ptr(), dp)
+        L = lbm13.lib()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        lbm13._check(L.lbm13_set_state(lat.handle, *ptrs), lat.handle)
+        lat.step(args.steps)
+        lbm13._check(L.lbm13_moments(lat.handle, outp, mask), lat.handle)
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * n * n * args.steps / float(tt.item()) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * 8 * n * n / args.steps, "d2h_bytes_per_step": 4 * 8 * n * n / args.steps,
+               "note": f"per job: upload (rho,ux,uy,T) from pinned host, {args.steps} steps, download the same 4 fields"}
+        del host, out
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    fp64 = None
+    if not args.no_fp64 and prec != lbm13.FP64:
+        lat = lbm13.Lattice(n, n, p, W.boundary(), precision=lbm13.FP64)
+        f = device_fields()
+        lat.set_state_device(*f)
+        del f
+        lat.step(3)
+        ms64 = time_steps(lat, args.fp64_steps, torch)
+        s64 = ms64 / 1e3 / args.fp64_steps
+        fp64 = {"value": n * n / s64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * s64, "steps": args.fp64_steps,
+                "bytes_per_lu": 208, "hbm_gbs": 208 * n * n / s64 / 1e9,
+                "hbm_frac": 208 * n * n / s64 / 1e9 / peak}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import build as ob
+        ob.build()
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
+            "config": {"workload": f"periodic shear wave {n}x{n} (throughput sweep), u_x = 0.01 sin(2 pi y/n)",
+                       "nu": NU, "Pr": PR, "precision": "fp32-deviation" if elem == 4 else "fp64",
+                       "bytes_per_lu": bytes_lu, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"inputs larger than L2 ({2 * 13 * elem * n * n / 1e9:.1f} GB of populations)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "step_kernel (fused pull-stream + walls + MRT collision)"},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "fp64": fp64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

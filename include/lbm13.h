@@ -1,0 +1,240 @@
+/*
+ * lbm13.h -- C ABI of the GB300 (sm_103a) D2Q13 energy-conserving multiple-
+ * relaxation-time lattice Boltzmann time step of Lallemand & Dubois,
+ * "Comparison of Simulations of Convective Flows" (Commun. Comput. Phys. 2015).
+ *
+ * One time step (lbm13_step) streams the 13 populations -- the D2Q9 set plus
+ * the four distance-2 links of Sec. 2, Eq. (d2q13-vitesses) -- applies the wall
+ * rules of Sec. 7, Eq. (d2q13-cl-abb) at the domain edges, and relaxes the nine
+ * non-conserved moments of the orthogonal basis of Sec. 2, Eq.
+ * (d2q13-polynomes) toward the equilibria of Eq. (d2q13-moments-equil), with
+ * the forcing of Sec. 5 / Sec. 8.  All of it runs in one fused CUDA kernel per
+ * step; the read-outs (lbm13_moments, lbm13_residual) are CUDA kernels too.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an lbm13_status (int); no C++ exception crosses the
+ *    ABI.  On failure lbm13_last_error(h) holds a message.
+ *  - Lattice arrays are row-major [ny][nx] (x fastest), in double precision.
+ *    Population arrays are [13][ny][nx], population j in the paper's order:
+ *    (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1) (2,0) (0,2)
+ *    (-2,0) (0,-2).  Moment planes are in the order rho, E, eps, varpi, jx,
+ *    jy, qx, qy, rx, ry, XX, XY, XXe.
+ *  - Host pointers are owned by the caller and only read or written during
+ *    the call (those calls synchronise the lattice's stream).  Device
+ *    pointers (the *_device calls) are owned by the caller and used in stream
+ *    order on the lattice's stream; the call returns before the work ends.
+ *  - The library owns the lattice's device buffers and obtains them from the
+ *    caller's allocator (or cudaMalloc when none is given).  Calls on one
+ *    handle are stream-ordered and not thread-safe.
+ *  - Units are lattice units: spacing 1, time step 1.
+ */
+#ifndef LBM13_H
+#define LBM13_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM13_OK = 0,
+    LBM13_EINVAL = 1,    /* bad argument: sizes, rates outside (0,2), unpaired periodic sides, NULL */
+    LBM13_ENOMEM = 2,    /* the allocator returned NULL */
+    LBM13_EUNSTABLE = 3, /* derived relaxation time sigma_q <= 0 (Eq. d2q13-sigma-qx) */
+    LBM13_EDIVERGED = 4, /* a non-finite population was found by lbm13_residual */
+    LBM13_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+    LBM13_ECUDA = 6      /* a CUDA runtime call failed; see lbm13_last_error */
+} lbm13_status;
+
+typedef enum {
+    LBM13_FP64 = 0,          /* populations stored and computed in double */
+    LBM13_FP32_DEVIATION = 1 /* stored as f_j - w_j in float, computed in float;
+                                read-outs and reductions in double */
+} lbm13_precision;
+
+/* Free parameters of Sec. 2 (the list after Eq. (d2q13-sigma-qx)).  The rest
+ * follows from them: h1, k1, h2 (Eq. d2q13-diffusion), sigma_q, c_erho, c2
+ * (Eq. d2q13-sigma-qx), s = 1/(sigma + 1/2) (Eq. d2q13-henon), and the shear
+ * rate from the viscosity, sigma_XX = 104 nu / (13 c1 + 95 + 2 E0).  Rates of
+ * the y components equal those of the x components (s_qy = s_qx, s_ry = s_rx,
+ * s_XY = s_XX). */
+typedef struct {
+    double E0;        /* reference energy moment at rho = 1 */
+    double c1;        /* q equilibrium constant */
+    double k2;        /* r equilibrium E coefficient */
+    double c_epsE;    /* eps equilibrium E coefficient */
+    double c_vpi_rho; /* varpi equilibrium rho coefficient */
+    double c_vpi_E;   /* varpi equilibrium E coefficient */
+    double Pr;        /* Prandtl number: viscosity / decay rate of the entropy mode */
+    double nu;        /* kinematic (shear) viscosity */
+    double s_eps, s_vpi, s_r, s_XXe; /* free relaxation rates, each in (0, 2) */
+} lbm13_params;
+
+typedef enum {
+    LBM13_PERIODIC = 0,   /* opposite sides must both be periodic */
+    LBM13_WALL_BB = 1,    /* adiabatic no-slip wall: every crossing link bounces back (Sec. 9) */
+    LBM13_WALL_MIXED = 2  /* velocity + temperature wall: links normal to the wall use
+                             anti-bounce-back, diagonal links bounce-back (Sec. 7) */
+} lbm13_wall_kind;
+
+/* A wall lies half a link outside the first/last node.  u_t is its velocity
+ * along the wall (+x for south/north walls, +y for west/east walls); T is its
+ * temperature (used by LBM13_WALL_MIXED only).  The wall density is the
+ * linear extrapolation 1.5 rho(first node) - 0.5 rho(second node). */
+typedef struct {
+    int kind;   /* lbm13_wall_kind */
+    double u_t;
+    double T;
+} lbm13_wall;
+
+/* Sides and body force.  The force per node is F = (rho - rho_ref) (gx, gy):
+ * rho_ref = 0 gives the body force rho g of the Poiseuille test (Sec. 8),
+ * rho_ref = 1 the buoyancy force proportional to rho - rho_0 of Sec. 5. */
+typedef struct {
+    lbm13_wall west, east, south, north;
+    double gx, gy;
+    double rho_ref;
+} lbm13_boundary;
+
+/* Device-memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes, aligned to 256 bytes, or NULL; free releases it.  They are called from
+ * lbm13_create (two population buffers), lbm13_residual (first call: the
+ * reduction buffers), lbm13_set_state and lbm13_moments (a staging buffer,
+ * released before they return) and lbm13_destroy. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} lbm13_allocator;
+
+typedef struct lbm13_lattice *lbm13_t;
+
+/* Number of doubles written by lbm13_derive. */
+#define LBM13_DERIVED_COUNT 48
+
+/* Moment / field selection bits for lbm13_moments. Bits 0..12 select the 13
+ * moments of the stored post-collision state (order above); the others select
+ * derived fields. */
+#define LBM13_MOMENT(k) (1u << (k))
+#define LBM13_FIELD_UX (1u << 13)   /* (j_x - F_x/2) / rho */
+#define LBM13_FIELD_UY (1u << 14)   /* (j_y - F_y/2) / rho */
+#define LBM13_FIELD_T (1u << 15)    /* p / rho, p = (E + 28 rho)/26 - |j|^2/(2 rho) */
+#define LBM13_FIELD_P (1u << 16)    /* p */
+#define LBM13_FIELD_E_SEC7 (1u << 17) /* E - (13/2)(ux^2 + uy^2), the read-out printed in Sec. 7 */
+#define LBM13_ALL_MOMENTS 0x1FFFu
+
+/* Layout of the 16 doubles written by lbm13_residual. */
+enum {
+    LBM13_R_RESIDUAL = 0, /* max of the three below */
+    LBM13_R_UX = 1,       /* ||F^n - F^{n-K}||_2 / (K max(||F^n - mean||_2, 1e-6 sqrt(N))), F = ux */
+    LBM13_R_UY = 2,       /* same, F = uy */
+    LBM13_R_T = 3,        /* same, F = T */
+    LBM13_R_MASS = 4,     /* sum rho over the lattice */
+    LBM13_R_JX = 5,       /* sum j_x (stored post-collision moments) */
+    LBM13_R_JY = 6,       /* sum j_y */
+    LBM13_R_ENERGY = 7,   /* sum E */
+    LBM13_R_NUSSELT = 8,  /* (1/(ny kappa dT)) sum [ux (T - Tm) - kappa D_x T], kappa = nu/Pr,
+                             dT = T_west - T_east; 0 unless both are LBM13_WALL_MIXED with dT != 0 */
+    LBM13_R_ASYM_U = 9,   /* max |u(i,j) + u(nx-1-i, ny-1-j)| (Sec. 10, Fig. 14) */
+    LBM13_R_ASYM_T = 10,  /* max |(T - Tm)(i,j) + (T - Tm)(mirror)| */
+    LBM13_R_UMAX = 11,    /* max |u| */
+    LBM13_R_NONFINITE = 12, /* number of non-finite stored populations */
+    LBM13_R_K = 13,       /* steps since the previous lbm13_residual (0 on the first call) */
+    LBM13_R_STEP = 14,    /* time step counter */
+    LBM13_R_TMEAN = 15    /* mean T */
+};
+
+/* Library version string (static storage). */
+const char *lbm13_version(void);
+
+/* Message for a status code (static storage). */
+const char *lbm13_status_string(int status);
+
+/* Host-only: derived constants of Sec. 2 for a parameter set, no GPU needed.
+ * out[LBM13_DERIVED_COUNT] receives: 0 A = 13c1+95+2E0, 1 B = 114404+51051c1-11492c_epsE+7854E0,
+ * 2 h1, 3 k1, 4 h2, 5 c2, 6 c_erho, 7 sigma_XX, 8 sigma_q, 9..21 the 13 rates s_k
+ * (0 for rho, E, jx, jy), 22..34 the rest populations w_j = f_eq(rho=1, E=E0, j=0),
+ * 35 T0 = (E0 + 28)/26, 36 adiabatic sound speed squared A/52, 37 kappa = nu/Pr.
+ * Returns LBM13_EINVAL for a NULL argument or a rate outside (0, 2) and
+ * LBM13_EUNSTABLE when sigma_q <= 0 (out is filled in both cases). */
+int lbm13_derive(const lbm13_params *params, double *out);
+
+/* Create an nx x ny lattice (nx, ny >= 2; >= 4 along an axis that has walls;
+ * nx <= 2^20, ny <= 32768, nx * ny < 2^31) on the current CUDA device.  `alloc` may be NULL (cudaMalloc),
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  The state starts
+ * at rest: rho = 1, u = 0, T = T0.  On success *out is a new handle. */
+int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary,
+                 int precision, const lbm13_allocator *alloc, void *stream, lbm13_t *out);
+
+/* Release the device buffers (through the allocator) and the handle.  NULL is a no-op. */
+void lbm13_destroy(lbm13_t h);
+
+/* Last error message of this handle (static storage per handle). */
+const char *lbm13_last_error(lbm13_t h);
+
+/* Change the stream the following calls are ordered on. */
+int lbm13_set_stream(lbm13_t h, void *stream);
+
+/* Lattice geometry: out[0] nx, out[1] ny, out[2] pitch (elements per row of a
+ * population plane), out[3] precision, out[4] bytes per stored population,
+ * out[5] device bytes held, out[6] time step counter. */
+int lbm13_info(lbm13_t h, int64_t out[8]);
+
+/* Set the state to the equilibrium of the given fields (host arrays [ny][nx];
+ * any NULL field takes its rest value: rho 1, u 0, T T0):
+ * f*_j = f_eq,j(rho, j = rho u, E = rho (26 T - 28) + 13 rho |u|^2).
+ * Resets the step counter and the residual snapshot. */
+int lbm13_set_state(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T);
+
+/* As lbm13_set_state, with device arrays (no NULLs), stream-ordered. */
+int lbm13_set_state_device(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T);
+
+/* Checkpoint: write / read the stored post-collision populations, host
+ * [13][ny][nx] doubles (in FP32-deviation mode converted from / to float
+ * deviations).  set_raw resets the residual snapshot and sets the step
+ * counter to `step`; get_raw returns the counter in *step when step != NULL. */
+int lbm13_set_raw_state(lbm13_t h, const double *f, int64_t step);
+int lbm13_get_raw_state(lbm13_t h, double *f, int64_t *step);
+
+/* Bit-exact checkpoint of the stored state (in the storage precision, as
+ * stored), for resuming a run.  lbm13_checkpoint_bytes gives the size of the
+ * image: a 64-byte header (magic "LBM13CK1", nx, ny, precision, pitch, step
+ * counter as int64) followed by the 13 population planes.  lbm13_save writes
+ * the image into a host buffer of at least that size; lbm13_restore reads one
+ * back into a lattice of the same nx, ny and precision (EINVAL otherwise) and
+ * resets the residual snapshot.  Both synchronise. */
+int lbm13_checkpoint_bytes(lbm13_t h, size_t *bytes);
+int lbm13_save(lbm13_t h, void *host, size_t bytes);
+int lbm13_restore(lbm13_t h, const void *host, size_t bytes);
+
+/* Advance n >= 0 time steps: one fused stream + wall + collide kernel each,
+ * launched on the lattice's stream (asynchronous). */
+int lbm13_step(lbm13_t h, int64_t n);
+
+/* Selected moments/fields of the stored state (mask bits above), planes of
+ * [ny][nx] doubles in increasing bit order, into a host buffer of
+ * popcount(mask) * nx * ny doubles (synchronises). */
+int lbm13_moments(lbm13_t h, double *out, unsigned mask);
+
+/* As lbm13_moments into a device buffer (stream-ordered, asynchronous). */
+int lbm13_moments_device(lbm13_t h, double *out, unsigned mask);
+
+/* FP64 reductions of the stored state into out[16] (host; layout above;
+ * synchronises).  Stores (ux, uy, T) as the snapshot for the next call.
+ * Returns LBM13_EDIVERGED (after filling out) when a population is not finite.
+ * The first call allocates the snapshot and reduction buffers. */
+int lbm13_residual(lbm13_t h, double *out);
+
+/* Time step counter. */
+int64_t lbm13_time(lbm13_t h);
+
+/* Wait for the lattice's stream. */
+int lbm13_synchronize(lbm13_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM13_H */

@@ -1,0 +1,611 @@
+// lbm13_api.cu -- the C ABI declared in include/lbm13.h: parameter derivation
+// (Sec. 2), lattice life cycle, state transfer and kernel dispatch.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm13.h"
+#include "lbm13_internal.h"
+
+using namespace lbm13;
+
+struct lbm13_lattice {
+    int nx = 0, ny = 0, precision = 0, device = 0;
+    long long pitch = 0, plane = 0;
+    size_t elem = 0, state_bytes = 0, bytes_held = 0;
+    lbm13_params p{};
+    lbm13_boundary b{};
+    lbm13_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    long long t = 0;
+    double derived[LBM13_DERIVED_COUNT] = {};
+    Coef<double> kd{};
+    Coef<float> kf{};
+    WallArgs<double> wd[4]{};
+    WallArgs<float> wf[4]{};
+    bool force = false;
+    // reductions
+    void *red_mem = nullptr;
+    ReduceBufs rb{};
+    double *out_dev = nullptr;
+    int have_snap = 0;
+    long long snap_t = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+const char *kVersion = "lbm13 1.0 (D2Q13 energy-conserving MRT, sm_103a)";
+
+int fail(lbm13_t h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(lbm13_t h, cudaError_t e, const char *where)
+{
+    return fail(h, LBM13_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+// Keeps the lattice's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+void *dev_alloc(lbm13_t h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(bytes, h->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) h->bytes_held += bytes;
+    return p;
+}
+
+void dev_free(lbm13_t h, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (h->has_alloc) h->alloc.free(p, h->alloc.ctx);
+    else cudaFree(p);
+    bytes = (bytes + 255) & ~size_t(255);
+    h->bytes_held -= bytes < h->bytes_held ? bytes : h->bytes_held;
+}
+
+bool finite_all(std::initializer_list<double> v)
+{
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// Sec. 2: Eqs. (d2q13-diffusion), (d2q13-sigma-qx), (d2q13-henon), and the shear
+// relaxation time sigma_XX = 104 nu / A of the basis.  Fills out[] and returns a
+// status: EINVAL for a rate outside (0, 2) or a non-positive viscosity, Prandtl
+// number or A; EUNSTABLE when sigma_q <= 0.
+int derive(const lbm13_params &p, double *out)
+{
+    for (int i = 0; i < LBM13_DERIVED_COUNT; ++i) out[i] = 0.0;
+    const double E0 = p.E0, c1 = p.c1, k2 = p.k2, ceE = p.c_epsE;
+    const double A = 13.0 * c1 + 95.0 + 2.0 * E0;
+    const double B = 114404.0 + 51051.0 * c1 - 11492.0 * ceE + 7854.0 * E0;
+    const double h1 = 17.0 / 26.0 - c1 / 2.0 - E0 / 13.0;
+    const double k1 = 2.0 / 13.0;
+    const double h2 = -(19.5 + 6.5 * c1 + E0) * k2 -
+                      7.0 / 624.0 * A * (874481.0 + 459459.0 * c1 - 103428.0 * ceE + 70686.0 * E0) / B;
+    const double sXX_sigma = 104.0 * p.nu / A;
+    const double sq_sigma = -654.5 * sXX_sigma * A / B;
+    const double cer = 140.0 + 28.0 * ceE + A * B / (22984.0 * p.Pr);
+    const double c2 = -65.0 / 24.0 - 21.0 / 8.0 * (c1 + h1 + k1 * E0) - k2 * E0 - h2;
+    const double sXX = 1.0 / (sXX_sigma + 0.5), sq = 1.0 / (sq_sigma + 0.5);
+    out[0] = A; out[1] = B; out[2] = h1; out[3] = k1; out[4] = h2; out[5] = c2; out[6] = cer;
+    out[7] = sXX_sigma; out[8] = sq_sigma;
+    double s[Q] = {0, 0, p.s_eps, p.s_vpi, 0, 0, sq, sq, p.s_r, p.s_r, sXX, sXX, p.s_XXe};
+    for (int k = 0; k < Q; ++k) out[9 + k] = s[k];
+    // rest populations w = M^-1 (1, E0, eps0, varpi0, 0, ..., 0)
+    Mom<double> d{};
+    d.rho = 1.0 / kD[0];
+    d.E = E0 / kD[1];
+    d.eps = (cer + ceE * E0) / kD[2];
+    d.vpi = (p.c_vpi_rho + p.c_vpi_E * E0) / kD[3];
+    double w[Q] = {};
+    inverse_add<true>(d, w);
+    for (int j = 0; j < Q; ++j) out[22 + j] = w[j];
+    out[35] = (E0 + 28.0) / 26.0;
+    out[36] = A / 52.0;
+    out[37] = p.nu / p.Pr;
+    if (!finite_all({E0, c1, k2, ceE, p.c_vpi_rho, p.c_vpi_E, p.Pr, p.nu, p.s_eps, p.s_vpi, p.s_r, p.s_XXe}))
+        return LBM13_EINVAL;
+    if (!(A > 0.0) || !(p.nu > 0.0) || !(p.Pr > 0.0) || B == 0.0) return LBM13_EINVAL;
+    if (!(sq_sigma > 0.0)) return LBM13_EUNSTABLE;
+    const int nc[9] = {2, 3, 6, 7, 8, 9, 10, 11, 12};
+    for (int i : nc)
+        if (!(s[i] > 0.0 && s[i] < 2.0)) return LBM13_EINVAL;
+    return LBM13_OK;
+}
+
+template <typename C>
+void fill_coef(lbm13_t h, Coef<C> &k)
+{
+    const double *D = h->derived;
+    const lbm13_params &p = h->p;
+    k.E0 = C(p.E0);
+    k.cer = C(D[6]);
+    k.ceE = C(p.c_epsE);
+    k.cwr = C(p.c_vpi_rho);
+    k.cwE = C(p.c_vpi_E);
+    k.h1 = C(D[2]);
+    k.k1 = C(D[3]);
+    k.Q10 = C(p.c1 + D[2] + D[3] * p.E0);
+    k.h2 = C(D[4]);
+    k.k2 = C(p.k2);
+    k.R10 = C(D[5] + D[4] + p.k2 * p.E0);
+    const double *s = D + 9;
+    k.l_eps = C(s[2] / kD[2]);
+    k.l_vpi = C(s[3] / kD[3]);
+    k.l_q = C(s[6] / kD[6]);
+    k.l_r = C(s[8] / kD[8]);
+    k.l_XX = C(s[10] / kD[10]);
+    k.l_XY = C(s[11] / kD[11]);
+    k.l_XXe = C(s[12] / kD[12]);
+    k.gx = C(h->b.gx);
+    k.gy = C(h->b.gy);
+    k.rho_ref = C(h->b.rho_ref);
+}
+
+template <typename C>
+void fill_walls(lbm13_t h, WallArgs<C> *w)
+{
+    const lbm13_wall *src[4] = {&h->b.west, &h->b.east, &h->b.south, &h->b.north};
+    for (int s = 0; s < 4; ++s) {
+        const lbm13_wall &in = *src[s];
+        WallArgs<C> &o = w[s];
+        o.kind = in.kind;
+        o.needs_data = in.kind == WALL_MIXED || (in.kind == WALL_BB && in.u_t != 0.0);
+        o.ux = C(s <= EAST ? 0.0 : in.u_t);
+        o.uy = C(s <= EAST ? in.u_t : 0.0);
+        o.base = C(26.0 * in.T - 28.0);
+        o.eT = C(26.0 * (in.T - (h->p.E0 + 28.0) / 26.0));
+    }
+}
+
+template <typename T>
+ReadArgs<T> read_args(lbm13_t h)
+{
+    ReadArgs<T> a;
+    a.f = static_cast<const T *>(h->buf[h->cur]);
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.rest.E0 = h->p.E0;
+    a.rest.eps0 = h->derived[6] + h->p.c_epsE * h->p.E0;
+    a.rest.vpi0 = h->p.c_vpi_rho + h->p.c_vpi_E * h->p.E0;
+    a.gx = h->b.gx;
+    a.gy = h->b.gy;
+    a.rho_ref = h->b.rho_ref;
+    return a;
+}
+
+template <typename T, typename C>
+int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
+{
+    StepArgs<T, C> a;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.per_x = h->b.west.kind == PERIODIC;
+    a.per_y = h->b.south.kind == PERIODIC;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.k = k;
+    for (int s = 0; s < 4; ++s) a.wall[s] = w[s];
+    for (long long i = 0; i < n; ++i) {
+        a.fin = static_cast<const T *>(h->buf[h->cur]);
+        a.fout = static_cast<T *>(h->buf[h->cur ^ 1]);
+        cudaError_t e = launch_step<T, C>(a, h->force, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBM13_OK;
+}
+
+int check_wall(const lbm13_wall &w)
+{
+    return (w.kind == PERIODIC || w.kind == WALL_BB || w.kind == WALL_MIXED) && std::isfinite(w.u_t) &&
+           std::isfinite(w.T);
+}
+
+unsigned popcount18(unsigned m)
+{
+    unsigned c = 0;
+    for (int b = 0; b < 18; ++b) c += (m >> b) & 1u;
+    return c;
+}
+
+int ensure_reduce(lbm13_t h)
+{
+    if (h->red_mem) return LBM13_OK;
+    const long long n = (long long)h->nx * h->ny;
+    const int nb = reduce_blocks(h->nx, h->ny);
+    const size_t doubles = size_t(6 * n) + size_t(nb) * kPartials + 16 + 16;
+    h->red_mem = dev_alloc(h, doubles * sizeof(double));
+    if (!h->red_mem) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the reduction buffers");
+    double *base = static_cast<double *>(h->red_mem);
+    h->rb.fields = base;
+    h->rb.snap = base + 3 * n;
+    h->rb.partials = base + 6 * n;
+    h->rb.stats = h->rb.partials + size_t(nb) * kPartials;
+    h->rb.nblocks = nb;
+    h->out_dev = h->rb.stats + 16;
+    return LBM13_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *lbm13_version(void) { return kVersion; }
+
+const char *lbm13_status_string(int status)
+{
+    switch (status) {
+    case LBM13_OK: return "ok";
+    case LBM13_EINVAL: return "invalid argument";
+    case LBM13_ENOMEM: return "out of device memory";
+    case LBM13_EUNSTABLE: return "unstable parameter set";
+    case LBM13_EDIVERGED: return "state diverged (non-finite populations)";
+    case LBM13_ETIMEOUT: return "device-side wait timed out";
+    case LBM13_ECUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+int lbm13_derive(const lbm13_params *params, double *out)
+{
+    if (!params || !out) return fail(nullptr, LBM13_EINVAL, "NULL argument");
+    return derive(*params, out);
+}
+
+const char *lbm13_last_error(lbm13_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary, int precision,
+                 const lbm13_allocator *alloc, void *stream, lbm13_t *out)
+{
+    if (!out) return fail(nullptr, LBM13_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || !boundary) return fail(nullptr, LBM13_EINVAL, "params or boundary is NULL");
+    if (precision != LBM13_FP64 && precision != LBM13_FP32_DEVIATION)
+        return fail(nullptr, LBM13_EINVAL, "precision must be LBM13_FP64 or LBM13_FP32_DEVIATION");
+    const lbm13_boundary &b = *boundary;
+    if (!check_wall(b.west) || !check_wall(b.east) || !check_wall(b.south) || !check_wall(b.north) ||
+        !finite_all({b.gx, b.gy, b.rho_ref}))
+        return fail(nullptr, LBM13_EINVAL, "bad wall kind or non-finite boundary data");
+    if ((b.west.kind == PERIODIC) != (b.east.kind == PERIODIC) || (b.south.kind == PERIODIC) != (b.north.kind == PERIODIC))
+        return fail(nullptr, LBM13_EINVAL, "opposite sides must both be periodic or both be walls");
+    const int min_x = b.west.kind == PERIODIC ? 2 : 4, min_y = b.south.kind == PERIODIC ? 2 : 4;
+    if (nx < min_x || ny < min_y || nx > (1 << 20) || ny > 32768 || (long long)nx * ny > 0x7fffffffLL)
+        return fail(nullptr, LBM13_EINVAL,
+                    "lattice size out of range (>= 2, >= 4 along a walled axis, nx <= 2^20, ny <= 32768, nx*ny < 2^31)");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM13_EINVAL, "allocator without alloc/free");
+
+    lbm13_t h = new lbm13_lattice();
+    h->nx = nx;
+    h->ny = ny;
+    h->precision = precision;
+    h->p = *params;
+    h->b = b;
+    if (alloc) { h->alloc = *alloc; h->has_alloc = true; }
+    h->stream = static_cast<cudaStream_t>(stream);
+    int st = derive(h->p, h->derived);
+    if (st != LBM13_OK) {
+        delete h;
+        return fail(nullptr, st, st == LBM13_EUNSTABLE ? "sigma_q <= 0: no positive relaxation time for q"
+                                                       : "parameter out of range (rates in (0,2), nu > 0, Pr > 0)");
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, LBM13_ECUDA, "no CUDA device");
+    }
+    fill_coef(h, h->kd);
+    fill_coef(h, h->kf);
+    fill_walls(h, h->wd);
+    fill_walls(h, h->wf);
+    h->force = h->b.gx != 0.0 || h->b.gy != 0.0;
+    h->elem = precision == LBM13_FP64 ? sizeof(double) : sizeof(float);
+    h->pitch = ((long long)nx + 31) / 32 * 32;
+    h->plane = (long long)ny * h->pitch;
+    h->state_bytes = size_t(Q) * size_t(h->plane) * h->elem;
+    for (int i = 0; i < 2; ++i) {
+        h->buf[i] = dev_alloc(h, h->state_bytes);
+        if (!h->buf[i]) {
+            lbm13_destroy(h);
+            return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the population buffers");
+        }
+    }
+    // deviation 0 everywhere = the rest state rho = 1, u = 0, T = T0
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = cudaMemsetAsync(h->buf[i], 0, h->state_bytes, h->stream);
+        if (e != cudaSuccess) {
+            lbm13_destroy(h);
+            return cuda_fail(nullptr, e, "cudaMemsetAsync");
+        }
+    }
+    *out = h;
+    return LBM13_OK;
+}
+
+void lbm13_destroy(lbm13_t h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i) dev_free(h, h->buf[i], h->state_bytes);
+    if (h->red_mem) {
+        const long long n = (long long)h->nx * h->ny;
+        dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
+    }
+    delete h;
+}
+
+int lbm13_set_stream(lbm13_t h, void *stream)
+{
+    if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
+    h->stream = static_cast<cudaStream_t>(stream);
+    return LBM13_OK;
+}
+
+int lbm13_info(lbm13_t h, int64_t out[8])
+{
+    if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
+    out[0] = h->nx;
+    out[1] = h->ny;
+    out[2] = h->pitch;
+    out[3] = h->precision;
+    out[4] = (int64_t)h->elem;
+    out[5] = (int64_t)h->bytes_held;
+    out[6] = h->t;
+    out[7] = 0;
+    return LBM13_OK;
+}
+
+int lbm13_set_state_device(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    if (!h || !rho || !ux || !uy || !T) return fail(h, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    cudaError_t e;
+    if (h->precision == LBM13_FP64)
+        e = launch_init<double>(static_cast<double *>(h->buf[h->cur]), h->nx, h->ny, h->pitch, h->plane, h->kd, rho,
+                                ux, uy, T, h->stream);
+    else
+        e = launch_init<float>(static_cast<float *>(h->buf[h->cur]), h->nx, h->ny, h->pitch, h->plane, h->kd, rho,
+                               ux, uy, T, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel launch");
+    h->t = 0;
+    h->have_snap = 0;
+    return LBM13_OK;
+}
+
+int lbm13_set_state(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
+    const size_t n = size_t(h->nx) * h->ny, bytes = n * sizeof(double);
+    double *stage = static_cast<double *>(dev_alloc(h, 4 * bytes));
+    if (!stage) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the state staging buffer");
+    const double *src[4] = {rho, ux, uy, T};
+    const double rest[4] = {1.0, 0.0, 0.0, (h->p.E0 + 28.0) / 26.0};
+    int rc = LBM13_OK;
+    std::vector<double> fill;
+    for (int q = 0; q < 4 && rc == LBM13_OK; ++q) {
+        const double *s = src[q];
+        if (!s) {
+            fill.assign(n, rest[q]);
+            s = fill.data();
+        }
+        cudaError_t e = cudaMemcpyAsync(stage + q * n, s, bytes, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && !src[q]) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemcpyAsync (state upload)");
+    }
+    if (rc == LBM13_OK) rc = lbm13_set_state_device(h, stage, stage + n, stage + 2 * n, stage + 3 * n);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (rc == LBM13_OK && e != cudaSuccess) rc = cuda_fail(h, e, "cudaStreamSynchronize (set_state)");
+    dev_free(h, stage, 4 * bytes);
+    return rc;
+}
+
+int lbm13_set_raw_state(lbm13_t h, const double *f, int64_t step)
+{
+    if (!h || !f) return fail(h, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    const double *w = h->derived + 22;
+    const size_t n = size_t(h->nx) * h->ny;
+    std::vector<unsigned char> host(h->state_bytes, 0);
+    for (int j = 0; j < Q; ++j)
+        for (int y = 0; y < h->ny; ++y)
+            for (int x = 0; x < h->nx; ++x) {
+                const double v = f[size_t(j) * n + size_t(y) * h->nx + x] - w[j];
+                const size_t at = size_t(j) * h->plane + size_t(y) * h->pitch + x;
+                if (h->precision == LBM13_FP64) reinterpret_cast<double *>(host.data())[at] = v;
+                else reinterpret_cast<float *>(host.data())[at] = float(v);
+            }
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->buf[h->cur], host.data(), h->state_bytes, cudaMemcpyHostToDevice));
+    h->t = step;
+    h->have_snap = 0;
+    return LBM13_OK;
+}
+
+int lbm13_get_raw_state(lbm13_t h, double *f, int64_t *step)
+{
+    if (!h || !f) return fail(h, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    const double *w = h->derived + 22;
+    const size_t n = size_t(h->nx) * h->ny;
+    std::vector<unsigned char> host(h->state_bytes);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(host.data(), h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < Q; ++j)
+        for (int y = 0; y < h->ny; ++y)
+            for (int x = 0; x < h->nx; ++x) {
+                const size_t at = size_t(j) * h->plane + size_t(y) * h->pitch + x;
+                const double v = h->precision == LBM13_FP64 ? reinterpret_cast<const double *>(host.data())[at]
+                                                            : double(reinterpret_cast<const float *>(host.data())[at]);
+                f[size_t(j) * n + size_t(y) * h->nx + x] = v + w[j];
+            }
+    if (step) *step = h->t;
+    return LBM13_OK;
+}
+
+int lbm13_checkpoint_bytes(lbm13_t h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(h, LBM13_EINVAL, "NULL argument");
+    *bytes = 64 + h->state_bytes;
+    return LBM13_OK;
+}
+
+static const char kMagic[8] = {'L', 'B', 'M', '1', '3', 'C', 'K', '1'};
+
+int lbm13_save(lbm13_t h, void *host, size_t bytes)
+{
+    if (!h || !host) return fail(h, LBM13_EINVAL, "NULL argument");
+    if (bytes < 64 + h->state_bytes) return fail(h, LBM13_EINVAL, "checkpoint buffer too small");
+    DeviceGuard g(h->device);
+    unsigned char *p = static_cast<unsigned char *>(host);
+    int64_t hdr[8] = {0, h->nx, h->ny, h->precision, h->pitch, h->t, 0, 0};
+    std::memcpy(hdr, kMagic, 8);
+    std::memcpy(p, hdr, 64);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(p + 64, h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToHost));
+    return LBM13_OK;
+}
+
+int lbm13_restore(lbm13_t h, const void *host, size_t bytes)
+{
+    if (!h || !host) return fail(h, LBM13_EINVAL, "NULL argument");
+    if (bytes < 64 + h->state_bytes) return fail(h, LBM13_EINVAL, "checkpoint image too small");
+    const unsigned char *p = static_cast<const unsigned char *>(host);
+    int64_t hdr[8];
+    std::memcpy(hdr, p, 64);
+    if (std::memcmp(hdr, kMagic, 8) != 0 || hdr[1] != h->nx || hdr[2] != h->ny || hdr[3] != h->precision ||
+        hdr[4] != h->pitch)
+        return fail(h, LBM13_EINVAL, "checkpoint image does not match this lattice");
+    DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->buf[h->cur], p + 64, h->state_bytes, cudaMemcpyHostToDevice));
+    h->t = hdr[5];
+    h->have_snap = 0;
+    return LBM13_OK;
+}
+
+int lbm13_step(lbm13_t h, int64_t n)
+{
+    if (!h || n < 0) return fail(h, LBM13_EINVAL, "NULL handle or negative step count");
+    if (n == 0) return LBM13_OK;
+    DeviceGuard g(h->device);
+    if (h->precision == LBM13_FP64) return do_steps<double, double>(h, n, h->kd, h->wd);
+    return do_steps<float, float>(h, n, h->kf, h->wf);
+}
+
+int lbm13_moments_device(lbm13_t h, double *out, unsigned mask)
+{
+    if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
+    if (mask == 0 || (mask >> 18) != 0) return fail(h, LBM13_EINVAL, "mask must select bits 0..17");
+    DeviceGuard g(h->device);
+    cudaError_t e = h->precision == LBM13_FP64 ? launch_moments<double>(read_args<double>(h), out, mask, h->stream)
+                                               : launch_moments<float>(read_args<float>(h), out, mask, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel launch");
+    return LBM13_OK;
+}
+
+int lbm13_moments(lbm13_t h, double *out, unsigned mask)
+{
+    if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
+    if (mask == 0 || (mask >> 18) != 0) return fail(h, LBM13_EINVAL, "mask must select bits 0..17");
+    DeviceGuard g(h->device);
+    const size_t bytes = size_t(popcount18(mask)) * h->nx * h->ny * sizeof(double);
+    double *stage = static_cast<double *>(dev_alloc(h, bytes));
+    if (!stage) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the moments staging buffer");
+    int rc = lbm13_moments_device(h, stage, mask);
+    if (rc == LBM13_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, stage, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "moments download");
+    } else {
+        cudaStreamSynchronize(h->stream);
+    }
+    dev_free(h, stage, bytes);
+    return rc;
+}
+
+int lbm13_residual(lbm13_t h, double *out)
+{
+    if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    int rc = ensure_reduce(h);
+    if (rc != LBM13_OK) return rc;
+    ReduceConf c{};
+    c.have_snap = h->have_snap;
+    c.K = h->t - h->snap_t;
+    c.step = h->t;
+    const bool walls_T = h->b.west.kind == WALL_MIXED && h->b.east.kind == WALL_MIXED;
+    c.nusselt = walls_T && h->b.west.T != h->b.east.T;
+    c.dT = h->b.west.T - h->b.east.T;
+    c.Tref = 0.5 * (h->b.west.T + h->b.east.T);
+    c.kappa = h->p.nu / h->p.Pr;
+    c.asym_walls = walls_T;
+    c.Tasym = c.Tref;
+    cudaError_t e = h->precision == LBM13_FP64
+                        ? launch_reduce<double>(read_args<double>(h), h->rb, c, h->out_dev, h->stream)
+                        : launch_reduce<float>(read_args<float>(h), h->rb, c, h->out_dev, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernel launch");
+    CK(h, cudaMemcpyAsync(out, h->out_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->have_snap = 1;
+    h->snap_t = h->t;
+    if (out[LBM13_R_NONFINITE] > 0.0) return fail(h, LBM13_EDIVERGED, "non-finite populations in the state");
+    return LBM13_OK;
+}
+
+int64_t lbm13_time(lbm13_t h) { return h ? h->t : -1; }
+
+int lbm13_synchronize(lbm13_t h)
+{
+    if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
+    DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM13_OK;
+}
+
+} // extern "C"

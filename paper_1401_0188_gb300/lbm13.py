@@ -1,0 +1,320 @@
+"""ctypes binding of the lbm13 C ABI (include/lbm13.h).
+
+Argument marshalling only: every step of the time step, the read-outs and the
+reductions run in the CUDA library.  The functions mirror the C names
+(lbm13_create, lbm13_step, ...); `Lattice` wraps one handle.  PyTorch supplies
+device memory (its caching allocator, through the C allocator callback) and
+streams.  The library must have been built (paper_1401_0188_gb300.build); a
+missing library is an error, there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+Q = 13
+PARAM_FIELDS = ("E0", "c1", "k2", "c_epsE", "c_vpi_rho", "c_vpi_E", "Pr", "nu",
+                "s_eps", "s_vpi", "s_r", "s_XXe")
+PERIODIC, WALL_BB, WALL_MIXED = 0, 1, 2
+FP64, FP32_DEVIATION = 0, 1
+DERIVED_COUNT = 48
+
+FIELD_UX, FIELD_UY, FIELD_T, FIELD_P, FIELD_E_SEC7 = 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17
+ALL_MOMENTS = 0x1FFF
+
+STATUS = {0: "LBM13_OK", 1: "LBM13_EINVAL", 2: "LBM13_ENOMEM", 3: "LBM13_EUNSTABLE",
+          4: "LBM13_EDIVERGED", 5: "LBM13_ETIMEOUT", 6: "LBM13_ECUDA"}
+
+# Symbols declared in include/lbm13.h.
+EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create", "lbm13_destroy",
+           "lbm13_last_error", "lbm13_set_stream", "lbm13_info", "lbm13_set_state", "lbm13_set_state_device",
+           "lbm13_set_raw_state", "lbm13_get_raw_state", "lbm13_checkpoint_bytes", "lbm13_save",
+           "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
+           "lbm13_residual", "lbm13_time", "lbm13_synchronize")
+
+
+class Lbm13Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in PARAM_FIELDS]
+
+
+class Wall(C.Structure):
+    _fields_ = [("kind", C.c_int), ("u_t", C.c_double), ("T", C.c_double)]
+
+
+class Boundary(C.Structure):
+    _fields_ = [("west", Wall), ("east", Wall), ("south", Wall), ("north", Wall),
+                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_1401_0188_gb300.build.build() first")
+    L = C.CDLL(path)
+    dp, vp, i64 = C.POINTER(C.c_double), C.c_void_p, C.c_int64
+    sig = {
+        "lbm13_version": (C.c_char_p, []),
+        "lbm13_status_string": (C.c_char_p, [C.c_int]),
+        "lbm13_derive": (C.c_int, [C.POINTER(Params), dp]),
+        "lbm13_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(Params), C.POINTER(Boundary), C.c_int,
+                                   C.POINTER(Allocator), vp, C.POINTER(vp)]),
+        "lbm13_destroy": (None, [vp]),
+        "lbm13_last_error": (C.c_char_p, [vp]),
+        "lbm13_set_stream": (C.c_int, [vp, vp]),
+        "lbm13_info": (C.c_int, [vp, C.POINTER(i64)]),
+        "lbm13_set_state": (C.c_int, [vp, dp, dp, dp, dp]),
+        "lbm13_set_state_device": (C.c_int, [vp, vp, vp, vp, vp]),
+        "lbm13_set_raw_state": (C.c_int, [vp, dp, i64]),
+        "lbm13_get_raw_state": (C.c_int, [vp, dp, C.POINTER(i64)]),
+        "lbm13_checkpoint_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "lbm13_save": (C.c_int, [vp, vp, C.c_size_t]),
+        "lbm13_restore": (C.c_int, [vp, vp, C.c_size_t]),
+        "lbm13_step": (C.c_int, [vp, i64]),
+        "lbm13_moments": (C.c_int, [vp, dp, C.c_uint]),
+        "lbm13_moments_device": (C.c_int, [vp, vp, C.c_uint]),
+        "lbm13_residual": (C.c_int, [vp, dp]),
+        "lbm13_time": (i64, [vp]),
+        "lbm13_synchronize": (C.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(status, h=None):
+    if status != 0:
+        msg = lib().lbm13_last_error(h)
+        raise Lbm13Error(status, msg.decode() if msg else "")
+
+
+def make_params(p):
+    return Params(*[float(p[n]) for n in PARAM_FIELDS])
+
+
+def wall(kind=PERIODIC, u_t=0.0, T=0.0):
+    return {"kind": kind, "u_t": u_t, "T": T}
+
+
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0):
+    w = lambda d: d if d is not None else wall()
+    return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
+            "gx": gx, "gy": gy, "rho_ref": rho_ref}
+
+
+def make_boundary(b):
+    mk = lambda d: Wall(int(d["kind"]), float(d.get("u_t", 0.0)), float(d.get("T", 0.0)))
+    return Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
+                    float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)))
+
+
+def lbm13_version():
+    return lib().lbm13_version().decode()
+
+
+def lbm13_derive(params):
+    """Derived constants of Sec. 2 (host only); returns (status, out[48])."""
+    out = np.zeros(DERIVED_COUNT)
+    p = make_params(params)
+    st = lib().lbm13_derive(C.byref(p), _dp(out))
+    return st, out
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations to PyTorch's caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+        self.live = {}
+
+        def _alloc(size, ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(size), device=self.device, stream=self.stream)
+            except RuntimeError:
+                return None
+            self.live[ptr] = size
+            return ptr
+
+        def _free(ptr, ctx):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = Allocator(self._a, self._f, None)
+
+
+class Lattice:
+    """One lattice handle.
+
+    params:    dict with the 12 free parameters (PARAM_FIELDS).
+    bnd:       dict from `boundary(...)` (default: fully periodic, no force).
+    precision: FP64 or FP32_DEVIATION.
+    stream:    a torch.cuda.Stream (default: torch's current stream).
+    allocator: "torch" (caching allocator) or None (cudaMalloc).
+    """
+
+    def __init__(self, nx, ny, params, bnd=None, precision=FP64, stream=None, allocator="torch", device=None):
+        import torch
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = dict(params)
+        self.bnd = bnd if bnd is not None else boundary()
+        self.precision = precision
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._alloc = _TorchAllocator(self.device, self.stream) if allocator == "torch" else None
+            h = C.c_void_p()
+            p, b = make_params(self.params), make_boundary(self.bnd)
+            st = lib().lbm13_create(self.nx, self.ny, C.byref(p), C.byref(b), int(precision),
+                                    C.byref(self._alloc.struct) if self._alloc else None,
+                                    C.c_void_p(self.stream.cuda_stream), C.byref(h))
+            _check(st)
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().lbm13_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self):
+        out = (C.c_int64 * 8)()
+        _check(lib().lbm13_info(self._h, out), self._h)
+        keys = ("nx", "ny", "pitch", "precision", "elem_bytes", "device_bytes", "step")
+        return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    @property
+    def t(self):
+        return int(lib().lbm13_time(self._h))
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().lbm13_set_stream(self._h, C.c_void_p(stream.cuda_stream)), self._h)
+
+    def set_state(self, rho=None, ux=None, uy=None, T=None):
+        """Equilibrium of host fields (scalars broadcast; None = rest value)."""
+        shape = (self.ny, self.nx)
+        arrs = []
+        for a in (rho, ux, uy, T):
+            if a is None:
+                arrs.append(None)
+            else:
+                arrs.append(np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape)))
+        ptrs = [_dp(a) if a is not None else None for a in arrs]
+        _check(lib().lbm13_set_state(self._h, *ptrs), self._h)
+
+    def set_state_device(self, rho, ux, uy, T):
+        """Equilibrium of device fields: torch float64 CUDA tensors of shape (ny, nx)."""
+        for a in (rho, ux, uy, T):
+            if not (a.is_cuda and a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()):
+                raise ValueError("fields must be contiguous float64 CUDA tensors")
+            if tuple(a.shape) != (self.ny, self.nx):
+                raise ValueError("field shape must be (ny, nx)")
+        _check(lib().lbm13_set_state_device(self._h, *[C.c_void_p(a.data_ptr()) for a in (rho, ux, uy, T)]),
+               self._h)
+
+    def set_raw_state(self, f, step=0):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(Q, self.ny, self.nx)
+        _check(lib().lbm13_set_raw_state(self._h, _dp(f), int(step)), self._h)
+
+    def get_raw_state(self):
+        f = np.zeros((Q, self.ny, self.nx))
+        st = C.c_int64()
+        _check(lib().lbm13_get_raw_state(self._h, _dp(f), C.byref(st)), self._h)
+        return f
+
+    def save(self):
+        """Bit-exact checkpoint image (bytes)."""
+        n = C.c_size_t()
+        _check(lib().lbm13_checkpoint_bytes(self._h, C.byref(n)), self._h)
+        buf = (C.c_ubyte * n.value)()
+        _check(lib().lbm13_save(self._h, buf, n.value), self._h)
+        return bytes(buf)
+
+    def restore(self, image):
+        buf = (C.c_ubyte * len(image)).from_buffer_copy(image)
+        _check(lib().lbm13_restore(self._h, buf, len(image)), self._h)
+
+    def step(self, n=1):
+        _check(lib().lbm13_step(self._h, int(n)), self._h)
+
+    def moments(self, mask=ALL_MOMENTS):
+        k = bin(mask & 0x3FFFF).count("1")
+        out = np.zeros((k, self.ny, self.nx))
+        _check(lib().lbm13_moments(self._h, _dp(out), int(mask)), self._h)
+        return out
+
+    def macro(self):
+        """(rho, ux, uy, T), each (ny, nx)."""
+        return self.moments(1 | FIELD_UX | FIELD_UY | FIELD_T)
+
+    def moments_device(self, out, mask=ALL_MOMENTS):
+        k = bin(mask & 0x3FFFF).count("1")
+        if not (out.is_cuda and out.element_size() == 8 and out.is_contiguous() and out.numel() >= k * self.nx * self.ny):
+            raise ValueError("out must be a contiguous float64 CUDA tensor with room for the selected planes")
+        _check(lib().lbm13_moments_device(self._h, C.c_void_p(out.data_ptr()), int(mask)), self._h)
+
+    def residual(self, raise_on_divergence=True):
+        out = np.zeros(16)
+        st = lib().lbm13_residual(self._h, _dp(out))
+        if st == 4 and not raise_on_divergence:
+            return out
+        _check(st, self._h)
+        return out
+
+    def synchronize(self):
+        _check(lib().lbm13_synchronize(self._h), self._h)

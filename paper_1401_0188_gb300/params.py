@@ -1,0 +1,43 @@
+"""Free-parameter sets for the D2Q13 scheme (host side).
+
+Sec. 2 leaves E0, c1, k2, c_epsE, c_varpirho, c_varpiE and the rates s_XX,
+s_r, s_eps, s_varpi, s_XXe free, chosen by scanning the dispersion relation;
+the paper prints no values.  `pstar` is one linearly stable choice: rest
+populations at weights (0.53, 0.049, 0.0175, 0.051) for the rest particle, the
+unit axes, the diagonals and the distance-2 axes (which fixes E0, eps0, varpi0
+as their moments), c1 = -1, k2 = 0.4, c_varpiE = 0.3,
+c_varpirho = varpi0 - c_varpiE E0, rates s_eps 0.6, s_varpi 1.25, s_r 1.2,
+s_XXe 1.0, and c_epsE solved so that eps_eq at rest stays eps0 once c_erho
+follows the Prandtl number (Eq. d2q13-sigma-qx).
+"""
+
+# Values of the E, eps and varpi polynomials of Eq. (d2q13-polynomes) on the
+# four velocity shells |v|^2 = 0, 1, 2, 4 (four velocities each but the first).
+_SHELL_E = (-28.0, -15.0, -2.0, 24.0)
+_SHELL_EPS = (140.0, -2.0, -67.0, 34.0)
+_SHELL_VPI = (-12.0, 8.0, -6.0, 1.0)
+_WEIGHTS = (0.53, 0.049, 0.0175, 0.051)
+
+
+def _shell_moment(row):
+    return row[0] * _WEIGHTS[0] + 4.0 * sum(r * w for r, w in zip(row[1:], _WEIGHTS[1:]))
+
+
+def pstar(nu=0.05, Pr=0.71):
+    E0 = _shell_moment(_SHELL_E)
+    eps0 = _shell_moment(_SHELL_EPS)
+    vpi0 = _shell_moment(_SHELL_VPI)
+    c1, k2, cvE = -1.0, 0.4, 0.3
+    A = 13.0 * c1 + 95.0 + 2.0 * E0
+    # c_erho(c) + c E0 = eps0 with c_erho = 140 + 28 c + A (B0 - 11492 c) / (22984 Pr)
+    B0 = 114404.0 + 51051.0 * c1 + 7854.0 * E0
+    const = 140.0 + A * B0 / (22984.0 * Pr) - eps0
+    slope = 28.0 - A * 11492.0 / (22984.0 * Pr) + E0
+    ceE = -const / slope
+    return {"E0": E0, "c1": c1, "k2": k2, "c_epsE": ceE, "c_vpi_rho": vpi0 - cvE * E0, "c_vpi_E": cvE,
+            "Pr": Pr, "nu": nu, "s_eps": 0.6, "s_vpi": 1.25, "s_r": 1.2, "s_XXe": 1.0}
+
+
+def rest_temperature(params):
+    """T0 = (E0 + 28) / 26: the temperature p / rho of the rest state."""
+    return (params["E0"] + 28.0) / 26.0

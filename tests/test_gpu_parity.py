@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA time step, through the C ABI, against the FP64 CPU
+oracle on the same seeded inputs.
+
+FP64 storage must match the oracle within 1e-10 max-abs on all 13 moments
+(after 1000 steps for the 64 x 64 shear wave).  FP32-deviation storage is held
+to stated per-quantity bounds.  Sizes span several 32-wide tiles with ragged
+tails, every wall kind and corner combination, forcing, and the read-outs."""
+import os
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1401_0188_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+NTH = max(1, (os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_0188_gb300 import build, lbm13
+    build.build()
+    lbm13.lib()
+    return lbm13
+
+
+def _T0(p):
+    return (p["E0"] + 28.0) / 26.0
+
+
+def _pair(L, nx, ny, p, bnd, precision=0):
+    o = O.Lattice(nx, ny, p, bnd, nthreads=NTH)
+    g = L.Lattice(nx, ny, p, bnd, precision=precision)
+    return o, g
+
+
+def _init_fields(o, g, fields):
+    o.set_equilibrium(*fields)
+    g.set_state(*fields)
+
+
+def _init_raw(o, g, f):
+    o.set_raw(f)
+    g.set_raw_state(f)
+
+
+def _maxdiff(a, b):
+    return float(np.abs(a - b).max())
+
+
+# ---------------------------------------------------------------- FP64 parity
+
+def test_shear_wave_64_fp64_1000_steps(L, pstar):
+    """64 x 64 periodic, equilibrium with u_x = 0.01 sin(2 pi y/64), nu = 0.05,
+    Pr = 0.71, 1000 steps: all 13 moments within 1e-10 of the oracle, and the
+    decay rate of the wave equals nu k^2."""
+    n = 64
+    o, g = _pair(L, n, n, pstar, W.boundary())
+    ux, uy = W.shear_wave(n, n, 0.01)
+    _init_fields(o, g, (1.0, ux, uy, _T0(pstar)))
+    s = np.sin(2 * np.pi * np.arange(n) / n)[:, None]
+    g.step(200)
+    a1 = 2 * np.mean(g.macro()[1] * s)
+    o.step(1000)
+    g.step(800)
+    d = _maxdiff(o.moments(), g.moments())
+    assert d <= TOL64, d
+    a2 = 2 * np.mean(g.macro()[1] * s)
+    k = 2 * np.pi / n
+    assert np.log(a2 / a1) / 800 == pytest.approx(-pstar["nu"] * k * k, rel=1e-4)
+
+
+def test_perturbed_populations_64_fp64_1000_steps(L, pstar):
+    """Same lattice from populations w_j (1 + 1e-4 N(0,1)), PCG64 seed 20260101."""
+    n = 64
+    o, g = _pair(L, n, n, pstar, W.boundary())
+    f = W.perturbed_populations(o.constants()["w"], n, n, 1e-4)
+    _init_raw(o, g, f)
+    o.step(1000)
+    g.step(1000)
+    d = _maxdiff(o.moments(), g.moments())
+    assert d <= TOL64, d
+
+
+def _cases(T0):
+    hot, cold = T0 + 0.005, T0 - 0.005
+    B, M, P = W.WALL_BB, W.WALL_MIXED, W.PERIODIC
+    return {
+        "cavity": (48, 40, W.cavity(T0, 0.01, 2e-4)),
+        "couette": (37, 30, W.couette(T0, 0.05, 0.01)),
+        "poiseuille": (40, 33, W.poiseuille(1e-5)),
+        "lid_driven": (36, 36, W.boundary(west=W.wall(B), east=W.wall(B), south=W.wall(B),
+                                          north=W.wall(B, 0.05))),
+        "all_mixed_moving": (34, 29, W.boundary(west=W.wall(M, -0.02, hot), east=W.wall(M, 0.03, cold),
+                                                south=W.wall(M, 0.04, T0), north=W.wall(M, -0.01, hot),
+                                                gx=1e-4, gy=-2e-4, rho_ref=1.0)),
+        "x_walls_periodic_y": (35, 33, W.boundary(west=W.wall(M, 0.01, hot), east=W.wall(B, -0.02),
+                                                  gx=0.0, gy=1e-5, rho_ref=0.0)),
+        "mixed_x_bb_y_moving": (66, 20, W.boundary(west=W.wall(M, 0.0, hot), east=W.wall(M, 0.0, cold),
+                                                   south=W.wall(B, 0.03), north=W.wall(B))),
+        "periodic_forced": (45, 50, W.boundary(gx=2e-5, gy=-1e-5, rho_ref=0.0)),
+        "tiny_walls": (4, 4, W.boundary(west=W.wall(M, 0.0, hot), east=W.wall(M, 0.0, cold),
+                                        south=W.wall(B, 0.02), north=W.wall(M, 0.01, T0))),
+        "tiny_periodic": (2, 3, W.boundary()),
+        "wide_ragged_cavity": (100, 70, W.cavity(T0, 0.01, 1e-4)),
+    }
+
+
+@pytest.mark.parametrize("case", list(_cases(0.576).keys()))
+def test_walls_and_forcing_fp64(L, pstar, case):
+    T0 = _T0(pstar)
+    nx, ny, bnd = _cases(T0)[case]
+    o, g = _pair(L, nx, ny, pstar, bnd)
+    f = W.perturbed_populations(o.constants()["w"], nx, ny, 1e-3, seed=zlib.crc32(case.encode()))
+    _init_raw(o, g, f)
+    steps = 300
+    o.step(steps)
+    g.step(steps)
+    d = _maxdiff(o.moments(), g.moments())
+    assert d <= TOL64, (case, d)
+
+
+@pytest.mark.parametrize("case", ["cavity", "couette", "lid_driven"])
+def test_walls_from_fields_fp64(L, pstar, case):
+    T0 = _T0(pstar)
+    nx, ny, bnd = _cases(T0)[case]
+    o, g = _pair(L, nx, ny, pstar, bnd)
+    fields = W.random_fields(nx, ny, T0, seed=11, du=0.01, drho=0.01, dT=0.005)
+    _init_fields(o, g, fields)
+    o.step(200)
+    g.step(200)
+    assert _maxdiff(o.moments(), g.moments()) <= TOL64
+
+
+# --------------------------------------------------------------- read-outs
+
+def test_macro_fields_and_residual_match_oracle(L, pstar):
+    T0 = _T0(pstar)
+    nx, ny, bnd = 48, 40, W.cavity(T0, 0.01, 2e-4)
+    o, g = _pair(L, nx, ny, pstar, bnd)
+    _init_fields(o, g, W.random_fields(nx, ny, T0, seed=5, du=0.01, drho=0.005, dT=0.003))
+    o.step(50)
+    g.step(50)
+    assert _maxdiff(o.macro(), g.macro()) <= TOL64
+    r_o, r_g = o.residual(), g.residual()
+    o.step(40)
+    g.step(40)
+    r_o, r_g = o.residual(), g.residual()
+    assert r_g[13] == 40 and r_g[14] == 90
+    for i in (0, 1, 2, 3, 8, 9, 10, 11, 15):
+        assert r_g[i] == pytest.approx(r_o[i], rel=1e-9, abs=1e-14), i
+    for i in (4, 5, 6, 7):
+        assert r_g[i] == pytest.approx(r_o[i], rel=1e-12, abs=1e-11), i
+    assert r_g[12] == 0.0
+
+
+def test_moment_mask_selects_planes(L, pstar):
+    n = 40
+    g = L.Lattice(n, 24, pstar)
+    g.set_state(*W.random_fields(n, 24, _T0(pstar), seed=3))
+    full = g.moments(L.ALL_MOMENTS | L.FIELD_UX | L.FIELD_UY | L.FIELD_T | L.FIELD_P | L.FIELD_E_SEC7)
+    sub = g.moments((1 << 1) | (1 << 5) | L.FIELD_T)
+    assert np.array_equal(sub, full[[1, 5, 15]])
+    rho, jx, jy, E = full[0], full[4], full[5], full[1]
+    assert np.allclose(full[13], jx / rho, rtol=0, atol=1e-15)
+    assert np.allclose(full[16], (E + 28 * rho) / 26 - (jx ** 2 + jy ** 2) / (2 * rho), atol=1e-14)
+    assert np.allclose(full[17], E - 6.5 * (full[13] ** 2 + full[14] ** 2), atol=1e-13)
+
+
+# ------------------------------------------------------------ checkpoints
+
+def test_checkpoint_resume_is_bit_identical(L, pstar):
+    T0 = _T0(pstar)
+    nx, ny, bnd = _cases(T0)["cavity"]
+    a = L.Lattice(nx, ny, pstar, bnd)
+    b = L.Lattice(nx, ny, pstar, bnd)
+    fields = W.random_fields(nx, ny, T0, seed=9, du=0.01, drho=0.005, dT=0.003)
+    a.set_state(*fields)
+    a.step(37)
+    b.restore(a.save())
+    assert b.t == 37
+    a.step(50)
+    b.step(50)
+    assert a.save() == b.save()
+    assert b.t == 87
+    # the FP64 population transfer round-trips to round-off
+    f = a.get_raw_state()
+    b.set_raw_state(f, step=a.t)
+    assert np.abs(b.get_raw_state() - f).max() < 1e-15
+    with pytest.raises(L.Lbm13Error):
+        L.Lattice(nx + 1, ny, pstar, bnd).restore(a.save())
+
+
+# --------------------------------------------------------------- FP32 mode
+
+FP32_TOL = {"rho": 2e-6, "u": 2e-6, "T": 2e-6}
+
+
+@pytest.mark.parametrize("case", ["shear", "cavity", "couette", "poiseuille", "lid_driven"])
+def test_fp32_deviation_within_stated_bounds(L, pstar, case):
+    """FP32-deviation storage against the FP64 oracle after 500 steps: rho, u
+    and T within the bounds in FP32_TOL (absolute, lattice units)."""
+    T0 = _T0(pstar)
+    if case == "shear":
+        nx = ny = 64
+        bnd = W.boundary()
+    else:
+        nx, ny, bnd = _cases(T0)[case]
+    o, g = _pair(L, nx, ny, pstar, bnd, precision=L.FP32_DEVIATION)
+    _init_fields(o, g, W.random_fields(nx, ny, T0, seed=21, du=0.01, drho=0.005, dT=0.003))
+    o.step(500)
+    g.step(500)
+    mo, mg = o.macro(), g.macro()
+    err = {"rho": _maxdiff(mo[0], mg[0]), "u": max(_maxdiff(mo[1], mg[1]), _maxdiff(mo[2], mg[2])),
+           "T": _maxdiff(mo[3], mg[3])}
+    print(case, err)
+    for k, v in err.items():
+        assert v <= FP32_TOL[k], (case, k, v)
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_invalid_arguments_are_rejected(L, pstar):
+    bad = [
+        (0, 8, W.boundary()),
+        (1, 8, W.boundary()),
+        (8, 3, W.boundary(south=W.wall(W.WALL_BB), north=W.wall(W.WALL_BB))),
+        (8, 8, W.boundary(west=W.wall(W.WALL_BB))),           # unpaired periodic side
+        (8, 8, W.boundary(west=W.wall(7), east=W.wall(7))),   # unknown kind
+        (8, 40000, W.boundary()),
+    ]
+    for nx, ny, b in bad:
+        with pytest.raises(L.Lbm13Error) as e:
+            L.Lattice(nx, ny, pstar, b)
+        assert e.value.status == 1
+    with pytest.raises(L.Lbm13Error) as e:
+        L.Lattice(8, 8, dict(pstar, c1=-0.5, E0=-12.0))
+    assert e.value.status == 3
+    g = L.Lattice(8, 8, pstar)
+    with pytest.raises(L.Lbm13Error):
+        g.step(-1)
+    f0 = g.get_raw_state()
+    g.step(0)
+    assert np.array_equal(g.get_raw_state(), f0) and g.t == 0
+
+
+def test_rest_state_is_exact_fixed_point(L, pstar):
+    T0 = _T0(pstar)
+    for prec in (0, 1):
+        g = L.Lattice(33, 17, pstar, W.cavity(T0, 0.0, 0.0), precision=prec)
+        g.step(25)
+        m = g.macro()
+        assert np.abs(m[0] - 1).max() == 0.0 and np.abs(m[1]).max() == 0.0
+        assert np.abs(m[3] - T0).max() < 1e-15
+
+
+def test_divergence_is_reported(L, pstar):
+    g = L.Lattice(16, 16, pstar)
+    f = np.tile(O.Lattice(2, 2, pstar).constants()["w"][:, None, None], (1, 16, 16))
+    f[3, 5, 7] = np.nan
+    g.set_raw_state(f)
+    g.step(3)
+    with pytest.raises(L.Lbm13Error) as e:
+        g.residual()
+    assert e.value.status == 4
+    out = g.residual(raise_on_divergence=False)
+    assert out[12] > 0
+
+
+# ---------------------------------------------- full-size sampled checks
+
+def _tiled_fields(nx, ny, T0, seed):
+    """Seeded random 64 x 64 tile, repeated over the lattice, plus a shear wave."""
+    t = W.random_fields(64, 64, T0, seed, du=0.01, drho=0.005, dT=0.003)
+    reps = (ny // 64 + 1, nx // 64 + 1)
+    rho, ux, uy, T = [np.tile(a, reps)[:ny, :nx] for a in t]
+    ux = ux + W.shear_wave(nx, ny, 0.01)[0]
+    return rho, ux, uy, T
+
+
+@pytest.mark.parametrize("n,prec,steps", [(4096, 0, 2), (8192, 1, 2)])
+def test_full_size_sampled_nodes_match_oracle(L, pstar, n, prec, steps):
+    """Full-size periodic lattice in the bench's launch configuration: after
+    `steps` steps, sampled nodes equal the oracle's result on the (4 steps + 1)^2
+    patch of the same seeded fields around them (the dependence cone of a node
+    after `steps` pulls of reach 2)."""
+    import torch
+    T0 = _T0(pstar)
+    fields = _tiled_fields(n, n, T0, seed=31)
+    g = L.Lattice(n, n, pstar, precision=prec)
+    g.set_state(*fields)
+    g.step(steps)
+    full = g.moments(1 | L.FIELD_UX | L.FIELD_UY | L.FIELD_T)
+    del g
+    torch.cuda.empty_cache()
+    r = 2 * steps
+    rng = np.random.default_rng(77)
+    pts = [(0, 0), (n - 1, n - 1), (n // 2, 3)] + [tuple(rng.integers(0, n, 2)) for _ in range(5)]
+    tol = TOL64 if prec == 0 else 2e-6
+    for (x, y) in pts:
+        xs = [(x + d) % n for d in range(-r, r + 1)]
+        ys = [(y + d) % n for d in range(-r, r + 1)]
+        patch = [np.asarray(a)[np.ix_(ys, xs)] if np.ndim(a) else a for a in fields]
+        m = 2 * r + 1
+        o = O.Lattice(m, m, pstar)
+        o.set_equilibrium(*patch)
+        o.step(steps)
+        mo = o.macro()[:, r, r]
+        assert np.abs(mo - full[:, y, x]).max() <= tol, ((x, y), mo, full[:, y, x])
