@@ -96,18 +96,20 @@ def _cases(T0):
         "cavity": (48, 40, W.cavity(T0, 0.01, 2e-4)),
         "couette": (37, 30, W.couette(T0, 0.05, 0.01)),
         "poiseuille": (40, 33, W.poiseuille(1e-5)),
+        # moving walls stay inside the scheme's stability envelope (a 0.05 lid on
+        # 36 x 36 diverges after ~400 steps in the oracle and on the GPU alike)
         "lid_driven": (36, 36, W.boundary(west=W.wall(B), east=W.wall(B), south=W.wall(B),
-                                          north=W.wall(B, 0.05))),
-        "all_mixed_moving": (34, 29, W.boundary(west=W.wall(M, -0.02, hot), east=W.wall(M, 0.03, cold),
-                                                south=W.wall(M, 0.04, T0), north=W.wall(M, -0.01, hot),
-                                                gx=1e-4, gy=-2e-4, rho_ref=1.0)),
+                                          north=W.wall(B, 0.03))),
+        "all_mixed_moving": (34, 29, W.boundary(west=W.wall(M, -0.01, hot), east=W.wall(M, 0.015, cold),
+                                                south=W.wall(M, 0.02, T0), north=W.wall(M, -0.01, hot),
+                                                gx=1e-5, gy=-2e-5, rho_ref=1.0)),
         "x_walls_periodic_y": (35, 33, W.boundary(west=W.wall(M, 0.01, hot), east=W.wall(B, -0.02),
                                                   gx=0.0, gy=1e-5, rho_ref=0.0)),
         "mixed_x_bb_y_moving": (66, 20, W.boundary(west=W.wall(M, 0.0, hot), east=W.wall(M, 0.0, cold),
                                                    south=W.wall(B, 0.03), north=W.wall(B))),
         "periodic_forced": (45, 50, W.boundary(gx=2e-5, gy=-1e-5, rho_ref=0.0)),
         "tiny_walls": (4, 4, W.boundary(west=W.wall(M, 0.0, hot), east=W.wall(M, 0.0, cold),
-                                        south=W.wall(B, 0.02), north=W.wall(M, 0.01, T0))),
+                                        south=W.wall(B, 0.02), north=W.wall(M, 0.0, T0))),
         "tiny_periodic": (2, 3, W.boundary()),
         "wide_ragged_cavity": (100, 70, W.cavity(T0, 0.01, 1e-4)),
     }
@@ -200,7 +202,8 @@ def test_checkpoint_resume_is_bit_identical(L, pstar):
 
 # --------------------------------------------------------------- FP32 mode
 
-FP32_TOL = {"rho": 2e-6, "u": 2e-6, "T": 2e-6}
+# Stated bound of the FP32-deviation path (measured: <= 8.4e-9 on these cases)
+FP32_TOL = {"rho": 1e-7, "u": 1e-7, "T": 1e-7}
 
 
 @pytest.mark.parametrize("case", ["shear", "cavity", "couette", "poiseuille", "lid_driven"])
