@@ -233,6 +233,35 @@ int64_t lbm13_time(lbm13_t h);
 /* Wait for the lattice's stream. */
 int lbm13_synchronize(lbm13_t h);
 
+/* Largest lattice (nx * ny) that lbm13_totals_noalloc accepts. */
+#define LBM13_NOALLOC_MAX_NODES 67108864
+
+/* Conserved totals of the stored state without allocating anything.
+ * The paper has no counterpart; this is a service for callers that cannot
+ * allocate device memory when they need the totals: code running while a
+ * stream is captured in global mode (cudaMalloc fails there and invalidates
+ * the capture), serving loops whose device memory is all pre-reserved under a
+ * fixed budget by another allocator, and callbacks that must not re-enter the
+ * lattice's allocator.  lbm13_residual allocates on its first call; this call
+ * never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * out is a caller-owned DEVICE buffer of 8 doubles, written in stream order on
+ * the lattice's stream (the call returns before the work ends): 0 sum rho,
+ * 1 sum j_x, 2 sum j_y, 3 sum E (stored post-collision moments, as
+ * LBM13_R_MASS..LBM13_R_ENERGY of lbm13_residual), 4 number of non-finite
+ * populations, 5 max |u|, 6 mean T, 7 nx * ny.
+ *
+ * Scratch: a file-scope device array of 256 KiB (4096 x 8 doubles) that every
+ * GPU loading the library holds until the process exits; lattices of up to
+ * LBM13_NOALLOC_MAX_NODES nodes fit (larger ones return LBM13_EINVAL).  The
+ * first call on a device looks up that array's device address with the device
+ * current; make that first call before any stream capture.  Every call reuses
+ * the same array and each call's blocks overwrite their rows before they are
+ * read, so nothing needs clearing; calls whose work overlaps on the GPU (other
+ * streams, other lattices) race on it.  Returns LBM13_EINVAL for a NULL
+ * argument or an oversized lattice, LBM13_ECUDA if a launch fails. */
+int lbm13_totals_noalloc(lbm13_t h, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -609,3 +609,21 @@ int lbm13_synchronize(lbm13_t h)
 }
 
 } // extern "C"
+
+bool lbm13_state_view(const lbm13_lattice *h, lbm13::StateView *v)
+{
+    if (!h || !v) return false;
+    v->f = h->buf[h->cur];
+    v->nx = h->nx;
+    v->ny = h->ny;
+    v->precision = h->precision;
+    v->device = h->device;
+    v->pitch = h->pitch;
+    v->plane = h->plane;
+    v->E0 = h->p.E0;
+    v->gx = h->b.gx;
+    v->gy = h->b.gy;
+    v->rho_ref = h->b.rho_ref;
+    v->stream = h->stream;
+    return true;
+}

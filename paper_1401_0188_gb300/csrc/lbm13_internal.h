@@ -90,4 +90,18 @@ template <typename T>
 cudaError_t launch_reduce(const ReadArgs<T> &a, const ReduceBufs &b, const ReduceConf &c, double *out_dev,
                           cudaStream_t s);
 
+// Read-only view of a lattice handle (population buffer, layout, rest
+// constants, stream), for entry points that live outside lbm13_api.cu.
+struct StateView {
+    const void *f;
+    int nx, ny, precision, device;
+    long long pitch, plane;
+    double E0, gx, gy, rho_ref;
+    cudaStream_t stream;
+};
+
 } // namespace lbm13
+
+struct lbm13_lattice;
+// Fills *v from a handle; returns false for a NULL handle.
+bool lbm13_state_view(const lbm13_lattice *h, lbm13::StateView *v);

@@ -32,7 +32,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_last_error", "lbm13_set_stream", "lbm13_info", "lbm13_set_state", "lbm13_set_state_device",
            "lbm13_set_raw_state", "lbm13_get_raw_state", "lbm13_checkpoint_bytes", "lbm13_save",
            "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
-           "lbm13_residual", "lbm13_time", "lbm13_synchronize")
+           "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_totals_noalloc")
 
 
 class Lbm13Error(RuntimeError):
@@ -102,6 +102,7 @@ def lib():
         "lbm13_residual": (C.c_int, [vp, dp]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
+        "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
