@@ -233,6 +233,43 @@ int64_t lbm13_time(lbm13_t h);
 /* Wait for the lattice's stream. */
 int lbm13_synchronize(lbm13_t h);
 
+/* ---------------------------------------------------------------- plans
+ * A plan steps many lattices together: one batched launch per time step
+ * covers every tile of every lattice (uneven sizes, each with its own
+ * parameters, walls and force), and runs of 32 steps are replayed as CUDA
+ * graphs.  The per-node arithmetic is that of lbm13_step, so a lattice gives
+ * bit-identical results alone or in a plan.  Each lattice's step counter and
+ * buffers advance as with lbm13_step; the lattices must not be destroyed while
+ * a plan holds them, and their own streams are not used by the plan. */
+typedef struct lbm13_plan *lbm13_plan_t;
+
+/* Plan over `count` distinct lattices of one precision and device.  The plan's
+ * device table and work list come from `alloc` (NULL: cudaMalloc); `stream`
+ * orders the plan's launches.  Default tile: 32 x 8 nodes, 8 CTAs per SM,
+ * lattice-by-lattice order. */
+int lbm13_plan_create(const lbm13_t *lattices, int count, const lbm13_allocator *alloc, void *stream,
+                      lbm13_plan_t *out);
+void lbm13_plan_destroy(lbm13_plan_t p);
+const char *lbm13_plan_last_error(lbm13_plan_t p);
+
+/* Advance every lattice of the plan by n >= 0 steps (asynchronous). */
+int lbm13_plan_step(lbm13_plan_t p, int64_t n);
+
+/* Autotuner: times every candidate (rows per thread R and warps per block BY
+ * of the tile, persistent CTAs per SM or one CTA per tile, and the order of
+ * the tiles: by lattice, round robin, largest first) over steps_per_candidate
+ * real steps each (+1 warm-up), then keeps the fastest.  The steps taken count
+ * as simulation steps.  *best_ms_per_step (may be NULL) gets the best time. */
+int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step);
+
+/* Choose a configuration: (R, BY) in {(1,4), (2,4), (4,4), (2,2), (1,8)},
+ * ctas_per_sm 0 (one CTA per tile) .. 64, order 0 by lattice, 1 round robin,
+ * 2 largest first. */
+int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order);
+
+/* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried by the last tune. */
+int lbm13_plan_config(lbm13_plan_t p, int64_t out[8]);
+
 /* Largest lattice (nx * ny) that lbm13_totals_noalloc accepts. */
 #define LBM13_NOALLOC_MAX_NODES 67108864
 

@@ -1,5 +1,6 @@
 // lbm13_api.cu -- the C ABI declared in include/lbm13.h: parameter derivation
 // (Sec. 2), lattice life cycle, state transfer and kernel dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -30,6 +31,13 @@ struct lbm13_lattice {
     WallArgs<double> wd[4]{};
     WallArgs<float> wf[4]{};
     bool force = false;
+    // wall corrections written by the boundary-link kernel (when a wall needs data)
+    void *corr = nullptr;
+    size_t corr_bytes = 0;
+    bool any_wall_data = false;
+    // CUDA graphs of kGraphSteps steps, one per starting buffer parity
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     // reductions
     void *red_mem = nullptr;
     ReduceBufs rb{};
@@ -218,9 +226,14 @@ ReadArgs<T> read_args(lbm13_t h)
 }
 
 template <typename T, typename C>
-int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
+StepArgs<T, C> step_args(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C> *w)
 {
-    StepArgs<T, C> a;
+    StepArgs<T, C> a{};
+    a.fin = static_cast<const T *>(h->buf[cur]);
+    a.fout = static_cast<T *>(h->buf[cur ^ 1]);
+    a.corr = static_cast<C *>(h->corr);
+    a.corr_stride = h->nx > h->ny ? h->nx : h->ny;
+    a.any_wall_data = h->any_wall_data ? 1 : 0;
     a.nx = h->nx;
     a.ny = h->ny;
     a.per_x = h->b.west.kind == PERIODIC;
@@ -229,10 +242,46 @@ int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
     a.plane = h->plane;
     a.k = k;
     for (int s = 0; s < 4; ++s) a.wall[s] = w[s];
+    return a;
+}
+
+constexpr long long kGraphSteps = 32;  // even: a graph launch leaves the buffer parity unchanged
+
+// Captures kGraphSteps step launches starting from buffer `cur` into a graph.
+template <typename T, typename C>
+cudaError_t build_graph(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C> *w)
+{
+    cudaError_t e;
+    if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (long long i = 0; i < kGraphSteps && le == cudaSuccess; ++i)
+        le = launch_step<T, C>(step_args<T, C>(h, cur ^ int(i & 1), k, w), h->force, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[cur], g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+template <typename T, typename C>
+int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
+{
+    if (n >= kGraphSteps) {
+        if (!h->gexec[h->cur]) {
+            cudaError_t e = build_graph<T, C>(h, h->cur, k, w);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step graph capture");
+        }
+        for (; n >= kGraphSteps; n -= kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch (steps)");
+            h->t += kGraphSteps;
+        }
+    }
     for (long long i = 0; i < n; ++i) {
-        a.fin = static_cast<const T *>(h->buf[h->cur]);
-        a.fout = static_cast<T *>(h->buf[h->cur ^ 1]);
-        cudaError_t e = launch_step<T, C>(a, h->force, h->stream);
+        cudaError_t e = launch_step<T, C>(step_args<T, C>(h, h->cur, k, w), h->force, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
         h->cur ^= 1;
         h->t += 1;
@@ -354,6 +403,20 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
             return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the population buffers");
         }
     }
+    for (int s = 0; s < 4; ++s) h->any_wall_data = h->any_wall_data || h->wd[s].needs_data;
+    if (h->any_wall_data) {
+        h->corr_bytes = size_t(corr_count(nx, ny)) * h->elem;
+        h->corr = dev_alloc(h, h->corr_bytes);
+        if (!h->corr) {
+            lbm13_destroy(h);
+            return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the wall corrections");
+        }
+        cudaError_t e = cudaMemsetAsync(h->corr, 0, h->corr_bytes, h->stream);
+        if (e != cudaSuccess) {
+            lbm13_destroy(h);
+            return cuda_fail(nullptr, e, "cudaMemsetAsync (wall corrections)");
+        }
+    }
     // deviation 0 everywhere = the rest state rho = 1, u = 0, T = T0
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = cudaMemsetAsync(h->buf[i], 0, h->state_bytes, h->stream);
@@ -371,7 +434,11 @@ void lbm13_destroy(lbm13_t h)
     if (!h) return;
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i)
+        if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (int i = 0; i < 2; ++i) dev_free(h, h->buf[i], h->state_bytes);
+    dev_free(h, h->corr, h->corr_bytes);
     if (h->red_mem) {
         const long long n = (long long)h->nx * h->ny;
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
@@ -627,3 +694,367 @@ bool lbm13_state_view(const lbm13_lattice *h, lbm13::StateView *v)
     v->stream = h->stream;
     return true;
 }
+
+// ------------------------------------------------------------------ plans
+//
+// A plan steps many lattices with one batched launch per time step.  The
+// device table holds every lattice's arguments for both buffer parities; the
+// work list holds (lattice, tile) pairs in the order chosen by the tuner.
+
+struct lbm13_plan {
+    std::vector<lbm13_t> lats;
+    int precision = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    lbm13_allocator alloc{};
+    bool has_alloc = false;
+    void *desc = nullptr;
+    size_t desc_bytes = 0;
+    void *work = nullptr;
+    size_t work_bytes = 0;
+    int ntiles = 0;
+    void *wlats = nullptr;  // indices of the lattices whose walls need data
+    size_t wlats_bytes = 0;
+    int nwlats = 0;
+    long long nodes = 0;
+    std::vector<int> cur0;
+    int parity = 0;  // parity of the next launch relative to cur0
+    int R = 2, BY = 4, ctas = 8, order = 0, grid = 0, sms = 0, tried = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+int pfail(lbm13_plan_t p, int code, const std::string &msg)
+{
+    if (p) p->err = msg;
+    g_err = msg;
+    return code;
+}
+
+void *plan_alloc(lbm13_plan_t p, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void *ptr = nullptr;
+    if (p->has_alloc) ptr = p->alloc.alloc(bytes, p->alloc.ctx);
+    else if (cudaMalloc(&ptr, bytes) != cudaSuccess) { cudaGetLastError(); ptr = nullptr; }
+    return ptr;
+}
+
+void plan_free(lbm13_plan_t p, void *ptr)
+{
+    if (!ptr) return;
+    if (p->has_alloc) p->alloc.free(ptr, p->alloc.ctx);
+    else cudaFree(ptr);
+}
+
+template <typename C> const Coef<C> &coef_of(lbm13_t h);
+template <> const Coef<double> &coef_of<double>(lbm13_t h) { return h->kd; }
+template <> const Coef<float> &coef_of<float>(lbm13_t h) { return h->kf; }
+template <typename C> const WallArgs<C> *walls_of(lbm13_t h);
+template <> const WallArgs<double> *walls_of<double>(lbm13_t h) { return h->wd; }
+template <> const WallArgs<float> *walls_of<float>(lbm13_t h) { return h->wf; }
+
+void plan_drop_graphs(lbm13_plan_t p)
+{
+    for (int i = 0; i < 2; ++i)
+        if (p->gexec[i]) { cudaGraphExecDestroy(p->gexec[i]); p->gexec[i] = nullptr; }
+}
+
+template <typename T, typename C>
+int plan_upload_descs(lbm13_plan_t p)
+{
+    std::vector<BatchDesc<T, C>> host(p->lats.size());
+    p->cur0.resize(p->lats.size());
+    for (size_t i = 0; i < p->lats.size(); ++i) {
+        lbm13_t h = p->lats[i];
+        host[i].a[0] = step_args<T, C>(h, h->cur, coef_of<C>(h), walls_of<C>(h));
+        host[i].a[1] = step_args<T, C>(h, h->cur ^ 1, coef_of<C>(h), walls_of<C>(h));
+        host[i].force = h->force ? 1 : 0;
+        host[i].tiles_x = (h->nx + 31) / 32;
+        p->cur0[i] = h->cur;
+    }
+    std::vector<int> wl;
+    for (size_t i = 0; i < p->lats.size(); ++i)
+        if (p->lats[i]->any_wall_data) wl.push_back(int(i));
+    p->nwlats = int(wl.size());
+    if (!wl.empty()) {
+        const size_t wb = wl.size() * sizeof(int);
+        if (!p->wlats || p->wlats_bytes < wb) {
+            plan_free(p, p->wlats);
+            p->wlats = plan_alloc(p, wb);
+            p->wlats_bytes = wb;
+            if (!p->wlats) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the wall list");
+        }
+        cudaError_t e = cudaMemcpyAsync(p->wlats, wl.data(), wb, cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("wall list upload: ") + cudaGetErrorString(e));
+    }
+    const size_t bytes = host.size() * sizeof(BatchDesc<T, C>);
+    if (!p->desc || p->desc_bytes < bytes) {
+        plan_free(p, p->desc);
+        p->desc = plan_alloc(p, bytes);
+        p->desc_bytes = bytes;
+        if (!p->desc) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan table");
+    }
+    cudaError_t e = cudaMemcpyAsync(p->desc, host.data(), bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
+    p->parity = 0;
+    plan_drop_graphs(p);
+    return LBM13_OK;
+}
+
+// Work list for tile rows of BY * R rows, in one of three orders:
+// 0 lattice by lattice, 1 round robin across lattices, 2 largest lattice first.
+int plan_build_work(lbm13_plan_t p)
+{
+    const int rows = p->R * p->BY;
+    const size_t L = p->lats.size();
+    std::vector<std::vector<int2>> per(L);
+    for (size_t i = 0; i < L; ++i) {
+        lbm13_t h = p->lats[i];
+        const int tx = (h->nx + 31) / 32, ty = (h->ny + rows - 1) / rows;
+        per[i].reserve(size_t(tx) * ty);
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) per[i].push_back(make_int2(int(i), y * tx + x));
+    }
+    std::vector<int2> work;
+    std::vector<size_t> idx(L);
+    for (size_t i = 0; i < L; ++i) idx[i] = i;
+    if (p->order == 2)
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return per[a].size() > per[b].size(); });
+    if (p->order == 1) {
+        size_t most = 0;
+        for (auto &v : per) most = std::max(most, v.size());
+        for (size_t k = 0; k < most; ++k)
+            for (size_t i = 0; i < L; ++i)
+                if (k < per[i].size()) work.push_back(per[i][k]);
+    } else {
+        for (size_t i : idx) work.insert(work.end(), per[i].begin(), per[i].end());
+    }
+    p->ntiles = int(work.size());
+    const size_t bytes = std::max<size_t>(work.size(), 1) * sizeof(int2);
+    if (!p->work || p->work_bytes < bytes) {
+        plan_free(p, p->work);
+        p->work = plan_alloc(p, bytes);
+        p->work_bytes = bytes;
+        if (!p->work) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the work list");
+    }
+    cudaError_t e = cudaMemcpyAsync(p->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("work list upload: ") + cudaGetErrorString(e));
+    p->grid = p->ctas <= 0 ? p->ntiles : std::min(p->ntiles, p->sms * p->ctas);
+    if (p->grid < 1) p->grid = 1;
+    plan_drop_graphs(p);
+    return LBM13_OK;
+}
+
+cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
+{
+    cudaError_t e;
+    if (p->precision == LBM13_FP64) {
+        const auto *d = static_cast<const BatchDesc<double, double> *>(p->desc);
+        e = launch_batch_walls<double, double>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
+        if (e != cudaSuccess) return e;
+        return launch_batch<double, double>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
+                                            p->grid, s);
+    }
+    const auto *d = static_cast<const BatchDesc<float, float> *>(p->desc);
+    e = launch_batch_walls<float, float>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
+    if (e != cudaSuccess) return e;
+    return launch_batch<float, float>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY, p->grid,
+                                      s);
+}
+
+// Re-upload the table when a lattice was stepped or reset outside the plan.
+int plan_sync_parity(lbm13_plan_t p)
+{
+    for (size_t i = 0; i < p->lats.size(); ++i)
+        if (p->lats[i]->cur != (p->cur0[i] ^ p->parity))
+            return p->precision == LBM13_FP64 ? plan_upload_descs<double, double>(p) : plan_upload_descs<float, float>(p);
+    return LBM13_OK;
+}
+
+void plan_advance(lbm13_plan_t p, long long n)
+{
+    for (lbm13_t h : p->lats) {
+        h->cur ^= int(n & 1);
+        h->t += n;
+    }
+    p->parity ^= int(n & 1);
+}
+
+int plan_steps(lbm13_plan_t p, long long n)
+{
+    int rc = plan_sync_parity(p);
+    if (rc != LBM13_OK) return rc;
+    if (n >= kGraphSteps) {
+        if (!p->gexec[p->parity]) {
+            cudaError_t e = cudaSuccess;
+            if (!p->cap_stream) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan graph capture: ") + cudaGetErrorString(e));
+            cudaError_t le = cudaSuccess;
+            for (long long i = 0; i < kGraphSteps && le == cudaSuccess; ++i)
+                le = plan_launch(p, p->parity ^ int(i & 1), p->cap_stream);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(p->cap_stream, &g);
+            if (le != cudaSuccess) e = le;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec[p->parity], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan graph: ") + cudaGetErrorString(e));
+        }
+        for (; n >= kGraphSteps; n -= kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(p->gexec[p->parity], p->stream);
+            if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("cudaGraphLaunch (plan): ") + cudaGetErrorString(e));
+            plan_advance(p, kGraphSteps);
+        }
+    }
+    for (long long i = 0; i < n; ++i) {
+        cudaError_t e = plan_launch(p, p->parity, p->stream);
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("batched step launch: ") + cudaGetErrorString(e));
+        plan_advance(p, 1);
+    }
+    return LBM13_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int lbm13_plan_create(const lbm13_t *lattices, int count, const lbm13_allocator *alloc, void *stream,
+                      lbm13_plan_t *out)
+{
+    if (!out) return pfail(nullptr, LBM13_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!lattices || count <= 0) return pfail(nullptr, LBM13_EINVAL, "empty lattice list");
+    if (alloc && (!alloc->alloc || !alloc->free)) return pfail(nullptr, LBM13_EINVAL, "allocator without alloc/free");
+    for (int i = 0; i < count; ++i) {
+        if (!lattices[i]) return pfail(nullptr, LBM13_EINVAL, "NULL lattice in the list");
+        if (lattices[i]->precision != lattices[0]->precision || lattices[i]->device != lattices[0]->device)
+            return pfail(nullptr, LBM13_EINVAL, "lattices of one plan must share precision and device");
+        for (int k = 0; k < i; ++k)
+            if (lattices[k] == lattices[i]) return pfail(nullptr, LBM13_EINVAL, "a lattice appears twice");
+    }
+    lbm13_plan_t p = new lbm13_plan();
+    p->lats.assign(lattices, lattices + count);
+    p->precision = lattices[0]->precision;
+    p->device = lattices[0]->device;
+    p->stream = static_cast<cudaStream_t>(stream);
+    if (alloc) { p->alloc = *alloc; p->has_alloc = true; }
+    DeviceGuard g(p->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) {
+        delete p;
+        return pfail(nullptr, LBM13_ECUDA, "cudaGetDeviceProperties");
+    }
+    p->sms = prop.multiProcessorCount;
+    for (lbm13_t h : p->lats) p->nodes += (long long)h->nx * h->ny;
+    // the lattices' own streams must be idle before the plan takes over
+    for (lbm13_t h : p->lats) cudaStreamSynchronize(h->stream);
+    int rc = p->precision == LBM13_FP64 ? plan_upload_descs<double, double>(p) : plan_upload_descs<float, float>(p);
+    if (rc == LBM13_OK) rc = plan_build_work(p);
+    if (rc != LBM13_OK) {
+        lbm13_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return LBM13_OK;
+}
+
+void lbm13_plan_destroy(lbm13_plan_t p)
+{
+    if (!p) return;
+    DeviceGuard g(p->device);
+    cudaStreamSynchronize(p->stream);
+    plan_drop_graphs(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    plan_free(p, p->desc);
+    plan_free(p, p->work);
+    plan_free(p, p->wlats);
+    delete p;
+}
+
+const char *lbm13_plan_last_error(lbm13_plan_t p) { return p ? p->err.c_str() : g_err.c_str(); }
+
+int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order)
+{
+    if (!p) return pfail(nullptr, LBM13_EINVAL, "NULL plan");
+    if (!batch_shape_supported(R, BY) || order < 0 || order > 2 || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return pfail(p, LBM13_EINVAL, "unsupported tile shape, order or CTA count");
+    DeviceGuard g(p->device);
+    p->R = R;
+    p->BY = BY;
+    p->ctas = ctas_per_sm;
+    p->order = order;
+    return plan_build_work(p);
+}
+
+int lbm13_plan_config(lbm13_plan_t p, int64_t out[8])
+{
+    if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");
+    out[0] = p->R;
+    out[1] = p->BY;
+    out[2] = p->ctas;
+    out[3] = p->order;
+    out[4] = p->ntiles;
+    out[5] = p->grid;
+    out[6] = p->nodes;
+    out[7] = p->tried;
+    return LBM13_OK;
+}
+
+int lbm13_plan_step(lbm13_plan_t p, int64_t n)
+{
+    if (!p || n < 0) return pfail(p, LBM13_EINVAL, "NULL plan or negative step count");
+    DeviceGuard g(p->device);
+    return plan_steps(p, n);
+}
+
+int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step)
+{
+    if (!p || steps_per_candidate < 1) return pfail(p, LBM13_EINVAL, "NULL plan or steps_per_candidate < 1");
+    DeviceGuard g(p->device);
+    static const int shapes[][2] = {{1, 4}, {2, 4}, {4, 4}, {2, 2}, {1, 8}};
+    static const int ctas[] = {0, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return pfail(p, LBM13_ECUDA, "cudaEventCreate");
+    double best = 1e300;
+    int bR = p->R, bBY = p->BY, bC = p->ctas, bO = p->order, rc = LBM13_OK;
+    p->tried = 0;
+    for (const auto &sh : shapes) {
+        for (int c : ctas) {
+            for (int o = 0; o < 3 && rc == LBM13_OK; ++o) {
+                p->R = sh[0];
+                p->BY = sh[1];
+                p->ctas = c;
+                p->order = o;
+                if ((rc = plan_build_work(p)) != LBM13_OK) break;
+                if ((rc = plan_steps(p, 1)) != LBM13_OK) break;  // warm-up
+                cudaEventRecord(e0, p->stream);
+                if ((rc = plan_steps(p, steps_per_candidate)) != LBM13_OK) break;
+                cudaEventRecord(e1, p->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = pfail(p, LBM13_ECUDA, "tuning event"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = double(ms) / steps_per_candidate;
+                ++p->tried;
+                if (per < best) { best = per; bR = sh[0]; bBY = sh[1]; bC = c; bO = o; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LBM13_OK) return rc;
+    p->R = bR;
+    p->BY = bBY;
+    p->ctas = bC;
+    p->order = bO;
+    if ((rc = plan_build_work(p)) != LBM13_OK) return rc;
+    if (best_ms_per_step) *best_ms_per_step = best;
+    return LBM13_OK;
+}
+
+} // extern "C"

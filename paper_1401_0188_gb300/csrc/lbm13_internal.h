@@ -24,16 +24,53 @@ struct WallArgs {
     C eT;            // 26 T_w - 28 - E0 = 26 (T_w - T0)
 };
 
+// Links that enter the lattice across each side, four per side, in a fixed
+// order (the slot of a wall correction):
+//   west (1, 5, 8, 9), east (3, 6, 7, 11), south (2, 5, 6, 10), north (4, 7, 8, 12).
+LBM13_HD constexpr int wall_link(int side, int i)
+{
+    return side == 0 ? (i == 0 ? 1 : i == 1 ? 5 : i == 2 ? 8 : 9)
+         : side == 1 ? (i == 0 ? 3 : i == 1 ? 6 : i == 2 ? 7 : 11)
+         : side == 2 ? (i == 0 ? 2 : i == 1 ? 5 : i == 2 ? 6 : 10)
+                     : (i == 0 ? 4 : i == 1 ? 7 : i == 2 ? 8 : 12);
+}
+LBM13_HD constexpr int wall_slot(int side, int j)
+{
+    return wall_link(side, 0) == j ? 0 : wall_link(side, 1) == j ? 1 : wall_link(side, 2) == j ? 2
+         : wall_link(side, 3) == j ? 3 : -1;
+}
+// The diagonal entering the lattice at each corner: 0 (x=0, y=0) j=5,
+// 1 (x=nx-1, y=0) j=6, 2 (x=0, y=ny-1) j=8, 3 (x=nx-1, y=ny-1) j=7.
+LBM13_HD constexpr int corner_link(int c) { return c == 0 ? 5 : c == 1 ? 6 : c == 2 ? 8 : 7; }
+
 template <typename T, typename C>
-struct StepArgs {
+struct alignas(16) StepArgs {
     const T *__restrict__ fin;
     T *__restrict__ fout;
+    // Wall corrections, written by the boundary-link kernel before each step:
+    // corr[(side * corr_stride + pos) * 4 + slot] is the term added to the
+    // reflected population of the link in `slot` at position `pos` along the
+    // side (2 f_eq,odd for bounce-back, 2 f_eq,even for anti-bounce-back), and
+    // corr[16 * corr_stride + c] that of corner c.  Only sides that need wall
+    // data (temperature walls, moving walls) are written and read.
+    C *corr;
+    int corr_stride;  // max(nx, ny)
+    int any_wall_data;
     int nx, ny;
     int per_x, per_y;
     long long pitch;  // elements per row
     long long plane;  // elements per population plane (ny * pitch)
     Coef<C> k;
     WallArgs<C> wall[4];
+};
+
+// One lattice of a batched launch: its arguments for both buffer parities
+// (a[p].fin is the buffer read when the step's parity is p).
+template <typename T, typename C>
+struct BatchDesc {
+    StepArgs<T, C> a[2];
+    int force;    // nonzero when g != 0
+    int tiles_x;  // ceil(nx / 32)
 };
 
 // Rest moments used by the read-outs (double precision).
@@ -54,6 +91,24 @@ struct ReadArgs {
 // Launchers (return the cudaError_t of the launch).
 template <typename T, typename C>
 cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s);
+
+// Doubles/floats of wall corrections for an nx x ny lattice.
+inline long long corr_count(int nx, int ny) { return 16LL * (nx > ny ? nx : ny) + 4; }
+
+// Boundary-link kernel of one lattice (no-op when no wall needs data).
+template <typename T, typename C>
+cudaError_t launch_walls(const StepArgs<T, C> &a, cudaStream_t s);
+
+// Boundary-link kernel of a batch: one block per listed lattice.
+template <typename T, typename C>
+cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int *lats, int nlats, int parity, cudaStream_t s);
+
+// Tile shapes (rows per thread R, warps per block BY) of the batched kernel.
+bool batch_shape_supported(int R, int BY);
+
+template <typename T, typename C>
+cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int R, int BY,
+                         int grid, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_init(T *f, int nx, int ny, long long pitch, long long plane, const Coef<double> &k,

@@ -32,7 +32,9 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_last_error", "lbm13_set_stream", "lbm13_info", "lbm13_set_state", "lbm13_set_state_device",
            "lbm13_set_raw_state", "lbm13_get_raw_state", "lbm13_checkpoint_bytes", "lbm13_save",
            "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
-           "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_totals_noalloc")
+           "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
+           "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
+           "lbm13_plan_config", "lbm13_totals_noalloc")
 
 
 class Lbm13Error(RuntimeError):
@@ -103,6 +105,13 @@ def lib():
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
+        "lbm13_plan_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(Allocator), vp, C.POINTER(vp)]),
+        "lbm13_plan_destroy": (None, [vp]),
+        "lbm13_plan_last_error": (C.c_char_p, [vp]),
+        "lbm13_plan_step": (C.c_int, [vp, i64]),
+        "lbm13_plan_tune": (C.c_int, [vp, C.c_int, dp]),
+        "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "lbm13_plan_config": (C.c_int, [vp, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -319,3 +328,63 @@ class Lattice:
 
     def synchronize(self):
         _check(lib().lbm13_synchronize(self._h), self._h)
+
+
+def _pcheck(status, p=None):
+    if status != 0:
+        msg = lib().lbm13_plan_last_error(p)
+        raise Lbm13Error(status, msg.decode() if msg else "")
+
+
+class Plan:
+    """Batched stepping of many lattices (one launch per step, CUDA graphs for
+    runs of 32 steps).  The Lattice objects must outlive the plan."""
+
+    def __init__(self, lattices, stream=None, allocator="torch"):
+        import torch
+        if not lattices:
+            raise ValueError("empty lattice list")
+        self.lattices = list(lattices)
+        dev = self.lattices[0].device
+        with torch.cuda.device(dev):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            self._alloc = _TorchAllocator(dev, self.stream) if allocator == "torch" else None
+            arr = (C.c_void_p * len(self.lattices))(*[l.handle for l in self.lattices])
+            h = C.c_void_p()
+            _pcheck(lib().lbm13_plan_create(arr, len(self.lattices),
+                                            C.byref(self._alloc.struct) if self._alloc else None,
+                                            C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().lbm13_plan_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        _pcheck(lib().lbm13_plan_step(self._h, int(n)), self._h)
+
+    def tune(self, steps_per_candidate=4):
+        best = C.c_double()
+        _pcheck(lib().lbm13_plan_tune(self._h, int(steps_per_candidate), C.byref(best)), self._h)
+        return best.value
+
+    def set_config(self, R=2, BY=4, ctas_per_sm=8, order=0):
+        _pcheck(lib().lbm13_plan_set_config(self._h, int(R), int(BY), int(ctas_per_sm), int(order)), self._h)
+
+    def config(self):
+        out = (C.c_int64 * 8)()
+        _pcheck(lib().lbm13_plan_config(self._h, out), self._h)
+        keys = ("R", "BY", "ctas_per_sm", "order", "tiles", "grid", "nodes", "tried")
+        return {k: int(out[i]) for i, k in enumerate(keys)}

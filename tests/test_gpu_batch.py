@@ -1,0 +1,130 @@
+"""Batched stepping (plans): many uneven lattices in one launch per step give
+results bit-identical to the same lattices stepped alone, for every tile
+shape, grid size and tile order the autotuner can pick."""
+import numpy as np
+import pytest
+
+from paper_1401_0188_gb300 import pstar as product_pstar
+from paper_1401_0188_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_0188_gb300 import build, lbm13
+    build.build()
+    lbm13.lib()
+    return lbm13
+
+
+def _specs():
+    out = []
+    for i, (nx, ny, kind, nu, Pr) in enumerate([
+            (64, 64, "cavity", 0.05, 0.71), (96, 70, "cavity", 0.03, 0.6), (37, 30, "couette", 0.05, 0.71),
+            (40, 33, "poiseuille", 0.08, 0.8), (130, 45, "periodic", 0.02, 0.5), (4, 4, "box", 0.05, 0.71),
+            (200, 128, "cavity", 0.1, 0.9), (33, 257, "cavity", 0.04, 0.55)]):
+        p = product_pstar(nu, Pr)
+        T0 = (p["E0"] + 28) / 26
+        bnd = {"cavity": W.cavity(T0, 0.01, 1e-4), "couette": W.couette(T0, 0.02, 0.01),
+               "poiseuille": W.poiseuille(1e-5), "periodic": W.boundary(gx=1e-5, gy=-2e-5),
+               "box": W.boundary(west=W.wall(W.WALL_BB), east=W.wall(W.WALL_BB), south=W.wall(W.WALL_BB),
+                                 north=W.wall(W.WALL_BB, 0.02))}[kind]
+        out.append((nx, ny, p, bnd, W.random_fields(nx, ny, T0, seed=100 + i, du=0.01, drho=0.005, dT=0.003)))
+    return out
+
+
+def _twins(L, precision):
+    """Two identical sets of lattices; lattice i is pre-stepped i % 3 times so
+    buffer parities differ across the plan."""
+    a, b = [], []
+    for i, (nx, ny, p, bnd, fields) in enumerate(_specs()):
+        for group in (a, b):
+            g = L.Lattice(nx, ny, p, bnd, precision=precision)
+            g.set_state(*fields)
+            g.step(i % 3)
+            group.append(g)
+    return a, b
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        assert x.t == y.t
+        assert x.save() == y.save()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plan_equals_lattices_stepped_alone(L, precision):
+    a, b = _twins(L, precision)
+    plan = L.Plan(a)
+    plan.step(37)       # one 32-step graph + 5 single launches
+    for g in b:
+        g.step(37)
+    _same(a, b)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_every_configuration_is_bit_identical(L, precision):
+    a, b = _twins(L, precision)
+    plan = L.Plan(a)
+    for R, BY in ((1, 4), (2, 4), (4, 4), (2, 2), (1, 8)):
+        for ctas in (0, 1, 8):
+            for order in (0, 1, 2):
+                plan.set_config(R, BY, ctas, order)
+                c = plan.config()
+                assert (c["R"], c["BY"], c["ctas_per_sm"], c["order"]) == (R, BY, ctas, order)
+                plan.step(3)
+                for g in b:
+                    g.step(3)
+    _same(a, b)
+    plan.close()
+
+
+def test_tune_then_step(L):
+    a, b = _twins(L, 1)
+    plan = L.Plan(a)
+    t0 = a[0].t
+    best = plan.tune(2)
+    c = plan.config()
+    assert best > 0 and c["tried"] == 60
+    taken = a[0].t - t0
+    assert taken == c["tried"] * 3
+    plan.step(40)
+    for g in b:
+        g.step(taken + 40)
+    _same(a, b)
+    plan.close()
+
+
+def test_plan_follows_steps_taken_outside(L):
+    a, b = _twins(L, 0)
+    plan = L.Plan(a)
+    plan.step(5)
+    a[2].step(1)          # parity of one lattice changes behind the plan's back
+    a[5].set_state(*_specs()[5][4])
+    b[5].set_state(*_specs()[5][4])
+    plan.step(4)
+    for i, g in enumerate(b):
+        g.step(5 + 4 + (1 if i == 2 else 0) if i != 5 else 4)
+    _same(a, b)
+    plan.close()
+
+
+def test_plan_rejects_bad_lattice_lists(L):
+    p = product_pstar()
+    x = L.Lattice(16, 16, p)
+    y = L.Lattice(16, 16, p, precision=L.FP32_DEVIATION)
+    with pytest.raises(L.Lbm13Error):
+        L.Plan([x, y])
+    with pytest.raises(L.Lbm13Error):
+        L.Plan([x, x])
+    plan = L.Plan([x])
+    with pytest.raises(L.Lbm13Error):
+        plan.set_config(3, 4, 8, 0)
+    with pytest.raises(L.Lbm13Error):
+        plan.step(-1)
+    plan.close()
