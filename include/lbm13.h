@@ -89,6 +89,16 @@ typedef struct {
     double T;
 } lbm13_wall;
 
+/* Wall density of the velocity+temperature walls.  Sec. 7 estimates it "by
+ * extrapolation from values measured in the fluid": EXTRAPOLATE takes
+ * 1.5 rho(first node) - 0.5 rho(second node).  Those walls are not mass-tight
+ * (mass drifts slowly through them, ~1e-8 per step per node in a cavity), so
+ * ZERO_FLUX offers the density that makes the wall's net normal mass flux
+ * zero, estimated from the outgoing populations; the total mass is then
+ * conserved to round-off and steady states are reached. */
+#define LBM13_WALL_DENSITY_EXTRAPOLATE 0
+#define LBM13_WALL_DENSITY_ZERO_FLUX 1
+
 /* Sides and body force.  The force per node is F = (rho - rho_ref) (gx, gy):
  * rho_ref = 0 gives the body force rho g of the Poiseuille test (Sec. 8),
  * rho_ref = 1 the buoyancy force proportional to rho - rho_0 of Sec. 5. */
@@ -96,6 +106,7 @@ typedef struct {
     lbm13_wall west, east, south, north;
     double gx, gy;
     double rho_ref;
+    int wall_density;  /* LBM13_WALL_DENSITY_EXTRAPOLATE or LBM13_WALL_DENSITY_ZERO_FLUX */
 } lbm13_boundary;
 
 /* Device-memory provider.  alloc returns a device pointer of at least `bytes`

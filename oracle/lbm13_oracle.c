@@ -37,6 +37,12 @@
  *   R11 at a velocity+temperature wall the links normal to the wall use
  *      anti-bounce-back, the diagonal links bounce-back.
  *   R12 wall density rho_w = 1.5 rho(first node) - 0.5 rho(second node).
+ *   R12' (option) at a velocity+temperature wall, rho_w such that the wall's
+ *      normal links carry no net mass: every even moment of the wall
+ *      equilibrium is proportional to rho_w, so the anti-bounce-back links
+ *      return 2 rho_w e_j and rho_w = (sum of the outgoing normal
+ *      populations) / (e_unit + 2 e_two), e the even equilibrium parts at
+ *      unit density.
  *   R13 an adiabatic wall bounces every link back.
  *   R14 bounce-back off a moving wall adds -2 f^eq,odd_j(wall).
  *   R15 Nu = (1/(Ny kappa dT)) sum_nodes [u_x (T - Tm) - kappa D_x T], kappa = nu/Pr.
@@ -71,6 +77,7 @@ typedef struct { int kind; double u_t; double T; } orc_wall; /* 0 periodic, 1 ad
 typedef struct {
     orc_wall west, east, south, north;
     double gx, gy, rho_ref;
+    int wall_density; /* 0: R12 extrapolation; 1: R12' zero net mass flux at temperature walls */
 } orc_boundary;
 
 typedef struct {
@@ -255,6 +262,7 @@ void orc_collide_node(const orc_lattice *L, const double *f, double *fs) { colli
 /* ----------------------------------------------------------------- walls */
 
 typedef struct { double rho, E, ux, uy; } wall_state;
+static double feq_part(const orc_lattice *L, const wall_state *w, int j, int odd);
 
 static const orc_wall *wall_of(const orc_lattice *L, int side) /* 0 W, 1 E, 2 S, 3 N */
 {
@@ -285,6 +293,24 @@ static wall_state wall_data(const orc_lattice *L, const double *fs, int side, in
     double r0 = node_moment(L, fs, K_RHO, x0, y0), r1 = node_moment(L, fs, K_RHO, x1, y1);
     s.rho = 1.5 * r0 - 0.5 * r1;
     if (side <= 1) { s.ux = 0.0; s.uy = w->u_t; } else { s.ux = w->u_t; s.uy = 0.0; }
+    if (w->kind == 2 && L->b.wall_density == 1) {
+        /* R12': outgoing normal links of this side (velocities n and 2n,
+         * n the outward normal), the unit one from the first node, the
+         * distance-2 one from both nodes */
+        static const int nx_of[4] = {-1, 1, 0, 0}, ny_of[4] = {0, 0, -1, 1};
+        int j1 = -1, j2 = -1;
+        for (int j = 0; j < Q; ++j) {
+            if (vx_of[j] == nx_of[side] && vy_of[j] == ny_of[side]) j1 = j;
+            if (vx_of[j] == 2 * nx_of[side] && vy_of[j] == 2 * ny_of[side]) j2 = j;
+        }
+        size_t plane = (size_t)L->nx * L->ny;
+        double out = fs[j1 * plane + (size_t)y0 * L->nx + x0] + fs[j2 * plane + (size_t)y0 * L->nx + x0] +
+                     fs[j2 * plane + (size_t)y1 * L->nx + x1];
+        wall_state unit = s;
+        unit.rho = 1.0;
+        unit.E = (26.0 * w->T - 28.0) + 13.0 * (s.ux * s.ux + s.uy * s.uy);
+        s.rho = out / (feq_part(L, &unit, j1, 0) + 2.0 * feq_part(L, &unit, j2, 0));
+    }
     if (w->kind == 2) {
         s.E = s.rho * (26.0 * w->T - 28.0) + 13.0 * s.rho * (s.ux * s.ux + s.uy * s.uy);
     } else {

@@ -32,7 +32,7 @@ class _Wall(C.Structure):
 
 class _Boundary(C.Structure):
     _fields_ = [("west", _Wall), ("east", _Wall), ("south", _Wall), ("north", _Wall),
-                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double)]
+                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int)]
 
 
 _lib = None
@@ -94,16 +94,17 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0):
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
 
 
 def _mk_boundary(b):
     mk = lambda d: _Wall(int(d["kind"]), float(d.get("u_t", 0.0)), float(d.get("T", 0.0)))
     return _Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
-                     float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)))
+                     float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
+                     int(b.get("wall_density", 0)))
 
 
 class Lattice:

@@ -204,6 +204,8 @@ void fill_walls(lbm13_t h, WallArgs<C> *w)
         o.uy = C(s <= EAST ? in.u_t : 0.0);
         o.base = C(26.0 * in.T - 28.0);
         o.eT = C(26.0 * (in.T - (h->p.E0 + 28.0) / 26.0));
+        o.mass_flux = in.kind == WALL_MIXED && h->b.wall_density == LBM13_WALL_DENSITY_ZERO_FLUX;
+        o.wsum = C(h->derived[22 + 1] + 2.0 * h->derived[22 + 9]);
     }
 }
 
@@ -360,6 +362,8 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
     if (!check_wall(b.west) || !check_wall(b.east) || !check_wall(b.south) || !check_wall(b.north) ||
         !finite_all({b.gx, b.gy, b.rho_ref}))
         return fail(nullptr, LBM13_EINVAL, "bad wall kind or non-finite boundary data");
+    if (b.wall_density != LBM13_WALL_DENSITY_EXTRAPOLATE && b.wall_density != LBM13_WALL_DENSITY_ZERO_FLUX)
+        return fail(nullptr, LBM13_EINVAL, "wall_density must be LBM13_WALL_DENSITY_EXTRAPOLATE or _ZERO_FLUX");
     if ((b.west.kind == PERIODIC) != (b.east.kind == PERIODIC) || (b.south.kind == PERIODIC) != (b.north.kind == PERIODIC))
         return fail(nullptr, LBM13_EINVAL, "opposite sides must both be periodic or both be walls");
     const int min_x = b.west.kind == PERIODIC ? 2 : 4, min_y = b.south.kind == PERIODIC ? 2 : 4;

@@ -22,6 +22,8 @@ struct WallArgs {
     C ux, uy;        // wall velocity (tangential only)
     C base;          // 26 T_w - 28      (rho_w (26 T_w - 28) is E_w without kinetic part)
     C eT;            // 26 T_w - 28 - E0 = 26 (T_w - T0)
+    int mass_flux;   // temperature wall whose density makes the net normal mass flux zero
+    C wsum;          // w_unit + 2 w_two: rest populations of one unit and one distance-2 axis link
 };
 
 // Links that enter the lattice across each side, four per side, in a fixed

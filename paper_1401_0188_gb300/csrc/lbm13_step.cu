@@ -24,7 +24,8 @@
 // with anti-bounce-back on the links normal to a velocity+temperature wall and
 // bounce-back on its diagonal links and on every link of an adiabatic wall.
 // The wall state is rho_w = 1.5 rho(first node) - 0.5 rho(second node) (the
-// extrapolation of Sec. 7), u_w the wall velocity, and E_w from the wall
+// extrapolation of Sec. 7; optionally, at temperature walls, the density that
+// makes the wall's net normal mass flux zero), u_w the wall velocity, and E_w from the wall
 // temperature, E_w = rho_w (26 T_w - 28) + 13 rho_w |u_w|^2, or extrapolated
 // like rho_w at an adiabatic wall.  A diagonal that crosses two walls at a
 // corner bounces back with the mean of the two walls' states.
@@ -58,7 +59,22 @@ __device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[4])
         g0[j] = ld(a, j, x0, y0);
         g1[j] = ld(a, j, x1, y1);
     }
-    const C drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
+    C drho;
+    if (w.kind == WALL_MIXED && w.mass_flux) {
+        // every even moment of the wall equilibrium is proportional to rho_w,
+        // so the anti-bounce-back links return 2 rho_w e_j; rho_w balances the
+        // outgoing normal populations (unit link from the first node, the
+        // distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two)
+        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
+        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
+        C e[Q];
+        equilibrium_dev(C(0), w.eT + C(13) * (w.ux * w.ux + w.uy * w.uy), w.ux, w.uy, a.k, e);
+        const C ea = C(0.5) * (e[ja] + e[copp(ja)]), eb = C(0.5) * (e[jb] + e[copp(jb)]);
+        const C dout = g0[ja] + g0[jb] + g1[jb];
+        drho = (dout - ea - C(2) * eb) / (w.wsum + ea + C(2) * eb);
+    } else {
+        drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
+    }
     const C rho = C(1) + drho;
     C dE;
     if (w.kind == WALL_MIXED)

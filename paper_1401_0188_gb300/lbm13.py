@@ -19,6 +19,7 @@ PARAM_FIELDS = ("E0", "c1", "k2", "c_epsE", "c_vpi_rho", "c_vpi_E", "Pr", "nu",
                 "s_eps", "s_vpi", "s_r", "s_XXe")
 PERIODIC, WALL_BB, WALL_MIXED = 0, 1, 2
 FP64, FP32_DEVIATION = 0, 1
+WALL_DENSITY_EXTRAPOLATE, WALL_DENSITY_ZERO_FLUX = 0, 1
 DERIVED_COUNT = 48
 
 FIELD_UX, FIELD_UY, FIELD_T, FIELD_P, FIELD_E_SEC7 = 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17
@@ -53,7 +54,7 @@ class Wall(C.Structure):
 
 class Boundary(C.Structure):
     _fields_ = [("west", Wall), ("east", Wall), ("south", Wall), ("north", Wall),
-                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double)]
+                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -139,16 +140,17 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0):
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
 
 
 def make_boundary(b):
     mk = lambda d: Wall(int(d["kind"]), float(d.get("u_t", 0.0)), float(d.get("T", 0.0)))
     return Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
-                    float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)))
+                    float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
+                    int(b.get("wall_density", 0)))
 
 
 def lbm13_version():

@@ -44,27 +44,35 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0):
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
+    """wall_density: 0 extrapolated density at temperature walls, 1 zero net mass flux."""
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
 
 
-def cavity(T0, dT, g, rho_ref=1.0):
+def cavity(T0, dT, g, rho_ref=1.0, wall_density=0):
     """Differentially heated cavity (Sec. 10): hot west and cold east velocity+
     temperature walls at T0 +- dT/2, adiabatic south and north walls, buoyancy
     F = (rho - rho_ref) (0, -g)."""
     return boundary(west=wall(WALL_MIXED, 0.0, T0 + dT / 2), east=wall(WALL_MIXED, 0.0, T0 - dT / 2),
-                    south=wall(WALL_BB), north=wall(WALL_BB), gx=0.0, gy=-abs(g), rho_ref=rho_ref)
+                    south=wall(WALL_BB), north=wall(WALL_BB), gx=0.0, gy=-abs(g), rho_ref=rho_ref,
+                    wall_density=wall_density)
 
 
-def couette(T0, U, dT):
+def couette(T0, U, dT, wall_density=0):
     """Couette channel (Sec. 7): periodic in x, lower wall at rest at T0 - dT/2,
     upper wall moving at U at T0 + dT/2, both velocity+temperature walls."""
-    return boundary(south=wall(WALL_MIXED, 0.0, T0 - dT / 2), north=wall(WALL_MIXED, U, T0 + dT / 2))
+    return boundary(south=wall(WALL_MIXED, 0.0, T0 - dT / 2), north=wall(WALL_MIXED, U, T0 + dT / 2),
+                    wall_density=wall_density)
 
 
-def poiseuille(g):
-    """Poiseuille channel (Sec. 8): periodic in x, adiabatic walls at rest,
-    body force rho g along x."""
-    return boundary(south=wall(WALL_BB), north=wall(WALL_BB), gx=g, gy=0.0, rho_ref=0.0)
+def poiseuille(g, T0=None, dT=0.0, wall_density=0):
+    """Poiseuille channel (Sec. 8): periodic in x, walls at rest, body force
+    rho g along x.  With T0 given, the walls are velocity+temperature walls at
+    T0 -+ dT/2 (the Couette-type temperature profile of Sec. 8), which also
+    carry off the viscous heat; without, adiabatic bounce-back walls."""
+    if T0 is None:
+        return boundary(south=wall(WALL_BB), north=wall(WALL_BB), gx=g, gy=0.0, rho_ref=0.0)
+    return boundary(south=wall(WALL_MIXED, 0.0, T0 - dT / 2), north=wall(WALL_MIXED, 0.0, T0 + dT / 2),
+                    gx=g, gy=0.0, rho_ref=0.0, wall_density=wall_density)

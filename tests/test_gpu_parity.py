@@ -112,6 +112,13 @@ def _cases(T0):
                                         south=W.wall(B, 0.02), north=W.wall(M, 0.0, T0))),
         "tiny_periodic": (2, 3, W.boundary()),
         "wide_ragged_cavity": (100, 70, W.cavity(T0, 0.01, 1e-4)),
+        # temperature walls whose density zeroes the net normal mass flux
+        "cavity_zero_flux": (48, 40, W.cavity(T0, 0.01, 2e-4, wall_density=1)),
+        "couette_zero_flux": (37, 30, W.couette(T0, 0.03, 0.01, wall_density=1)),
+        "poiseuille_temperature_walls": (40, 33, W.poiseuille(1e-5, T0=T0, dT=0.01, wall_density=1)),
+        "all_mixed_zero_flux": (34, 29, W.boundary(west=W.wall(M, -0.01, hot), east=W.wall(M, 0.015, cold),
+                                                   south=W.wall(M, 0.02, T0), north=W.wall(M, -0.01, hot),
+                                                   gx=1e-5, gy=-2e-5, rho_ref=1.0, wall_density=1)),
     }
 
 
