@@ -38,6 +38,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--serving-requests", type=int, default=24)
     return ap.parse_args()
 
 
@@ -197,6 +201,81 @@ def time_steps(lat, steps, torch):
     return start.elapsed_time(end)  # ms
 
 
+def run_batched(args, torch):
+    """256 uneven cavities (sides 64..512, Ra 1e3..1e6, Pr 0.5..1.0) stepped in
+    one launch per step by an autotuned plan, FP32-deviation; against the same
+    lattices in FP64, each with its own launches."""
+    from paper_1401_0188_gb300 import lbm13, serving as S
+    reqs = S.batch_workload()
+    out = {"workload": "256 cavities, side uniform in {64,96,128,192,256,384,512}, Ra log-uniform [1e3,1e6], "
+                       "Pr uniform [0.5,1.0], seed 4242, from rest"}
+
+    def make(prec):
+        lats = []
+        for r in reqs:
+            nx, ny, p, bnd = S.request_setup(r)
+            g = lbm13.Lattice(nx, ny, p, bnd, precision=prec)
+            g.set_state(1.0, 0.0, 0.0, (p["E0"] + 28) / 26)
+            lats.append(g)
+        return lats
+
+    nodes = None
+    for prec, name in ((lbm13.FP32_DEVIATION, "fp32_plan"), (lbm13.FP64, "fp64_per_lattice")):
+        lats = make(prec)
+        nodes = sum(g.nx * g.ny for g in lats)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if name == "fp32_plan":
+            plan = lbm13.Plan(lats)
+            best = plan.tune(4)
+            plan.step(8)
+            torch.cuda.synchronize()
+            e0.record()
+            plan.step(args.batched_steps)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.batched_steps
+            out["tune"] = plan.config()
+            out["gpu_launches_per_step"] = 2
+            plan.close()
+        else:
+            steps = max(4, args.batched_steps // 20)
+            for g in lats:
+                g.step(2)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                for g in lats:
+                    g.step(1)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        out[name] = {"MLUPS": nodes / (ms / 1e3) / 1e6, "ms_per_step": ms}
+        for g in lats:
+            g.close()
+        del lats
+        torch.cuda.empty_cache()
+    out["nodes_per_step"] = nodes
+    out["speedup_vs_fp64_per_lattice"] = out["fp32_plan"]["MLUPS"] / out["fp64_per_lattice"]["MLUPS"]
+    return out
+
+
+def run_serving(args):
+    """A bounded Poisson trace of cavity and channel solves served to residual
+    1e-7 by continuous batching in FP32-deviation storage, and the same trace on
+    the plain FP64 one-lattice-per-launch path."""
+    from paper_1401_0188_gb300 import lbm13, serving as S
+    reqs = S.poisson_trace(args.serving_requests, rate=20.0, seed=5151, side_range=(64, 192),
+                           ra_range=(1e3, 1e5), tol=1e-7)
+    res32, sum32 = S.Server(lbm13.FP32_DEVIATION, hbm_budget=120e9, check_every=1000).run(reqs)
+    res64, sum64 = S.Server(lbm13.FP64, hbm_budget=120e9, check_every=1000, batched=False).run(reqs)
+    nu_err = max((abs(a.Nu - b.Nu) for a, b in zip(res32, res64) if a.kind == "cavity"), default=0.0)
+    return {"trace": f"{len(reqs)} requests, Poisson 20/s (seed 5151), alternating cavity/channel, side "
+                     "log-uniform 64..192, Ra log-uniform 1e3..1e5, Pr 0.71, residual 1e-7, budget 120 GB",
+            "fp32_batched": sum32, "fp64_per_lattice": sum64,
+            "p99_speedup": sum64["p99_tts_s"] / sum32["p99_tts_s"],
+            "nusselt_max_abs_err_fp32_vs_fp64": nu_err}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -298,6 +377,13 @@ def run_ours(args):
         del lat
         torch.cuda.empty_cache()
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, torch)
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import build as ob
@@ -320,6 +406,8 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp64": fp64,
+            "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(res))

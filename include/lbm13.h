@@ -138,10 +138,12 @@ typedef struct lbm13_lattice *lbm13_t;
 
 /* Layout of the 16 doubles written by lbm13_residual. */
 enum {
-    LBM13_R_RESIDUAL = 0, /* max of the three below */
-    LBM13_R_UX = 1,       /* ||F^n - F^{n-K}||_2 / (K max(||F^n - mean||_2, 1e-6 sqrt(N))), F = ux */
-    LBM13_R_UY = 2,       /* same, F = uy */
-    LBM13_R_T = 3,        /* same, F = T */
+    LBM13_R_RESIDUAL = 0, /* max(r_u, r_T): r_u = ||u^n - u^{n-K}||_2 / (K max(||u^n - mean u^n||_2, 1e-6 sqrt(N)))
+                             with the velocity u = (ux, uy) as one vector field over N nodes, K steps since
+                             the previous call; r_T the same for T */
+    LBM13_R_UX = 1,       /* the ux part of r_u: ||ux^n - ux^{n-K}||_2 / (K max(||u^n - mean u^n||_2, 1e-6 sqrt(N))) */
+    LBM13_R_UY = 2,       /* the uy part of r_u */
+    LBM13_R_T = 3,        /* r_T */
     LBM13_R_MASS = 4,     /* sum rho over the lattice */
     LBM13_R_JX = 5,       /* sum j_x (stored post-collision moments) */
     LBM13_R_JY = 6,       /* sum j_y */
@@ -280,6 +282,14 @@ int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int or
 
 /* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried by the last tune. */
 int lbm13_plan_config(lbm13_plan_t p, int64_t out[8]);
+
+/* FP64 reductions of every lattice of the plan, host out[count * 16] in the
+ * layout of lbm13_residual (lattice i at out + 16 i), with a single
+ * synchronisation of the plan's stream.  Each lattice's residual snapshot
+ * advances as with lbm13_residual (a lattice's first call allocates its
+ * reduction buffers through its own allocator).  Returns LBM13_EDIVERGED,
+ * after filling out, when a lattice holds non-finite populations. */
+int lbm13_plan_residual(lbm13_plan_t p, double *out);
 
 /* Largest lattice (nx * ny) that lbm13_totals_noalloc accepts. */
 #define LBM13_NOALLOC_MAX_NODES 67108864

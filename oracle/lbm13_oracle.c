@@ -47,7 +47,8 @@
  *   R14 bounce-back off a moving wall adds -2 f^eq,odd_j(wall).
  *   R15 Nu = (1/(Ny kappa dT)) sum_nodes [u_x (T - Tm) - kappa D_x T], kappa = nu/Pr.
  *   R16 asymmetry S_u = max |u(i,j) + u(nx-1-i, ny-1-j)|.
- *   R17 residual r_F = ||F^n - F^{n-K}||_2 / (K max(||F^n - mean F^n||_2, 1e-6 sqrt(N))).
+ *   R17 residual: r = max(r_u, r_T), r_u = ||u^n - u^{n-K}||_2 / (K max(||u^n - mean u^n||_2, 1e-6 sqrt(N)))
+ *      with the velocity u = (ux, uy) taken as one vector field, r_T the same for T.
  *   corners: a diagonal that crosses two walls at once bounces back with the
  *      mean of the two walls' data.
  *
@@ -567,7 +568,8 @@ static void kadd(ksum *k, double v)
 }
 
 /* Read-outs, out[16]:
- *  0 residual max_F r_F (R17), 1..3 r_ux, r_uy, r_T (0 on the first call),
+ *  0 residual max(r_u, r_T) (R17), 1..3 the ux and uy parts of r_u (each
+ *  over the velocity's variation) and r_T (0 on the first call),
  *  4..7 totals of rho, jx, jy, E of the stored state (Kahan sums),
  *  8 Nu (R15; 0 unless west and east are temperature walls with T_w != T_e),
  *  9 S_u, 10 S_T (R16, S_T on T - Tm), 11 max |u|, 12 count of non-finite
@@ -595,31 +597,34 @@ void orc_residual(orc_lattice *L, double *out)
         if (!isfinite(L->f[i])) nonfinite += 1.0;
     out[12] = nonfinite;
 
-    /* residual against the snapshot */
+    /* residual against the snapshot (R17): the velocity is one vector field */
     long K = L->t - L->snap_t;
     if (L->have_snap && K > 0) {
         const double *F[3] = {ux, uy, T};
-        double rmax = 0.0;
+        double num[3], den[3];
         for (int a = 0; a < 3; ++a) {
             double mean = 0.0;
             for (size_t i = 0; i < plane; ++i) mean += F[a][i];
             mean /= (double)plane;
-            double num = 0.0, den = 0.0;
+            num[a] = 0.0;
+            den[a] = 0.0;
             for (size_t i = 0; i < plane; ++i) {
                 double d = F[a][i] - L->snap[a * plane + i];
-                num += d * d;
+                num[a] += d * d;
                 double e = F[a][i] - mean;
-                den += e * e;
+                den[a] += e * e;
             }
-            num = sqrt(num);
-            den = sqrt(den);
-            /* a field whose RMS variation is below 1e-6 counts as flat at that scale */
-            double floor_ = 1e-6 * sqrt((double)plane);
-            double r = num / ((double)K * (den > floor_ ? den : floor_));
-            out[1 + a] = r;
-            if (r > rmax) rmax = r;
         }
-        out[0] = rmax;
+        /* a field whose RMS variation is below 1e-6 counts as flat at that scale */
+        double floor_ = 1e-6 * sqrt((double)plane);
+        double du = sqrt(den[0] + den[1]), dT = sqrt(den[2]);
+        du = du > floor_ ? du : floor_;
+        dT = dT > floor_ ? dT : floor_;
+        out[1] = sqrt(num[0]) / ((double)K * du);
+        out[2] = sqrt(num[1]) / ((double)K * du);
+        out[3] = sqrt(num[2]) / ((double)K * dT);
+        double ru = sqrt(num[0] + num[1]) / ((double)K * du);
+        out[0] = ru > out[3] ? ru : out[3];
     }
     out[13] = (double)(L->have_snap ? K : 0);
     out[14] = (double)L->t;

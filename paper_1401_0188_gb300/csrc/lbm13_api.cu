@@ -304,6 +304,30 @@ unsigned popcount18(unsigned m)
     return c;
 }
 
+ReduceConf reduce_conf(lbm13_t h)
+{
+    ReduceConf c{};
+    c.have_snap = h->have_snap;
+    c.K = h->t - h->snap_t;
+    c.step = h->t;
+    const bool walls_T = h->b.west.kind == WALL_MIXED && h->b.east.kind == WALL_MIXED;
+    c.nusselt = walls_T && h->b.west.T != h->b.east.T;
+    c.dT = h->b.west.T - h->b.east.T;
+    c.Tref = 0.5 * (h->b.west.T + h->b.east.T);
+    c.kappa = h->p.nu / h->p.Pr;
+    c.asym_walls = walls_T;
+    c.Tasym = c.Tref;
+    return c;
+}
+
+// The four reduction launches of one lattice, results to out_dev[16].
+cudaError_t launch_residual(lbm13_t h, double *out_dev, cudaStream_t s)
+{
+    const ReduceConf c = reduce_conf(h);
+    return h->precision == LBM13_FP64 ? launch_reduce<double>(read_args<double>(h), h->rb, c, out_dev, s)
+                                      : launch_reduce<float>(read_args<float>(h), h->rb, c, out_dev, s);
+}
+
 int ensure_reduce(lbm13_t h)
 {
     if (h->red_mem) return LBM13_OK;
@@ -646,20 +670,7 @@ int lbm13_residual(lbm13_t h, double *out)
     DeviceGuard g(h->device);
     int rc = ensure_reduce(h);
     if (rc != LBM13_OK) return rc;
-    ReduceConf c{};
-    c.have_snap = h->have_snap;
-    c.K = h->t - h->snap_t;
-    c.step = h->t;
-    const bool walls_T = h->b.west.kind == WALL_MIXED && h->b.east.kind == WALL_MIXED;
-    c.nusselt = walls_T && h->b.west.T != h->b.east.T;
-    c.dT = h->b.west.T - h->b.east.T;
-    c.Tref = 0.5 * (h->b.west.T + h->b.east.T);
-    c.kappa = h->p.nu / h->p.Pr;
-    c.asym_walls = walls_T;
-    c.Tasym = c.Tref;
-    cudaError_t e = h->precision == LBM13_FP64
-                        ? launch_reduce<double>(read_args<double>(h), h->rb, c, h->out_dev, h->stream)
-                        : launch_reduce<float>(read_args<float>(h), h->rb, c, h->out_dev, h->stream);
+    cudaError_t e = launch_residual(h, h->out_dev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernel launch");
     CK(h, cudaMemcpyAsync(out, h->out_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -716,6 +727,7 @@ struct lbm13_plan {
     void *work = nullptr;
     size_t work_bytes = 0;
     int ntiles = 0;
+    double *res_dev = nullptr;  // [count][16] results of lbm13_plan_residual
     void *wlats = nullptr;  // indices of the lattices whose walls need data
     size_t wlats_bytes = 0;
     int nwlats = 0;
@@ -977,6 +989,7 @@ void lbm13_plan_destroy(lbm13_plan_t p)
     plan_free(p, p->desc);
     plan_free(p, p->work);
     plan_free(p, p->wlats);
+    plan_free(p, p->res_dev);
     delete p;
 }
 
@@ -1014,6 +1027,34 @@ int lbm13_plan_step(lbm13_plan_t p, int64_t n)
     if (!p || n < 0) return pfail(p, LBM13_EINVAL, "NULL plan or negative step count");
     DeviceGuard g(p->device);
     return plan_steps(p, n);
+}
+
+int lbm13_plan_residual(lbm13_plan_t p, double *out)
+{
+    if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(p->device);
+    const size_t bytes = p->lats.size() * 16 * sizeof(double);
+    if (!p->res_dev) {
+        p->res_dev = static_cast<double *>(plan_alloc(p, bytes));
+        if (!p->res_dev) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan's residual buffer");
+    }
+    for (size_t i = 0; i < p->lats.size(); ++i) {
+        lbm13_t h = p->lats[i];
+        int rc = ensure_reduce(h);
+        if (rc != LBM13_OK) return pfail(p, rc, h->err);
+        cudaError_t e = launch_residual(h, p->res_dev + 16 * i, p->stream);
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan reduction launch: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMemcpyAsync(out, p->res_dev, bytes, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan residual download: ") + cudaGetErrorString(e));
+    bool bad = false;
+    for (size_t i = 0; i < p->lats.size(); ++i) {
+        p->lats[i]->have_snap = 1;
+        p->lats[i]->snap_t = p->lats[i]->t;
+        bad = bad || out[16 * i + LBM13_R_NONFINITE] > 0.0;
+    }
+    return bad ? pfail(p, LBM13_EDIVERGED, "non-finite populations in a lattice of the plan") : LBM13_OK;
 }
 
 int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step)

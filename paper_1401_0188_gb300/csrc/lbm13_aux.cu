@@ -272,18 +272,17 @@ __global__ void __launch_bounds__(kReduceThreads) finalize2_kernel(ReduceBufs b,
     __shared__ double res[9];
     combine_partials(b.partials, b.nblocks, 7, 2, res);
     if (threadIdx.x == 0) {
+        // the velocity is one vector field: both components over its variation
         const double floor_ = 1e-6 * sqrt(double(n));
-        double rmax = 0.0;
-        for (int q = 0; q < 3; ++q) {
-            double r = 0.0;
-            if (c.have_snap && c.K > 0) {
-                const double num = sqrt(res[q]), den = sqrt(res[3 + q]);
-                r = num / (double(c.K) * (den > floor_ ? den : floor_));
-            }
-            out[1 + q] = r;
-            rmax = fmax(rmax, r);
+        for (int q = 0; q < 4; ++q) out[q] = 0.0;
+        if (c.have_snap && c.K > 0) {
+            const double du = fmax(sqrt(res[3] + res[4]), floor_), dT = fmax(sqrt(res[5]), floor_);
+            const double K = double(c.K);
+            out[1] = sqrt(res[0]) / (K * du);
+            out[2] = sqrt(res[1]) / (K * du);
+            out[3] = sqrt(res[2]) / (K * dT);
+            out[0] = fmax(sqrt(res[0] + res[1]) / (K * du), out[3]);
         }
-        out[0] = rmax;
         const double *p1 = b.stats + 3;
         out[4] = double(n) + p1[0];
         out[5] = p1[1];

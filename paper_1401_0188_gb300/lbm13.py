@@ -35,7 +35,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
-           "lbm13_plan_config", "lbm13_totals_noalloc")
+           "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc")
 
 
 class Lbm13Error(RuntimeError):
@@ -113,6 +113,7 @@ def lib():
         "lbm13_plan_tune": (C.c_int, [vp, C.c_int, dp]),
         "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "lbm13_plan_config": (C.c_int, [vp, C.POINTER(i64)]),
+        "lbm13_plan_residual": (C.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -384,6 +385,15 @@ class Plan:
 
     def set_config(self, R=2, BY=4, ctas_per_sm=8, order=0):
         _pcheck(lib().lbm13_plan_set_config(self._h, int(R), int(BY), int(ctas_per_sm), int(order)), self._h)
+
+    def residual(self, raise_on_divergence=True):
+        """(count, 16) FP64 read-outs of every lattice, one synchronisation."""
+        out = np.zeros((len(self.lattices), 16))
+        st = lib().lbm13_plan_residual(self._h, _dp(out))
+        if st == 4 and not raise_on_divergence:
+            return out
+        _pcheck(st, self._h)
+        return out
 
     def config(self):
         out = (C.c_int64 * 8)()

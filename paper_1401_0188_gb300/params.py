@@ -41,3 +41,37 @@ def pstar(nu=0.05, Pr=0.71):
 def rest_temperature(params):
     """T0 = (E0 + 28) / 26: the temperature p / rho of the rest state."""
     return (params["E0"] + 28.0) / 26.0
+
+
+# Free-parameter sets found by stability.search (Nelder-Mead on the linear
+# stability scan at background speeds up to 0.03), as raw search vectors
+# (x0, x1, x2, x3, c1, k2, c_varpiE, s_eps, s_varpi, s_r, s_XXe); see
+# stability.make_params for the mapping.  Scanned stable (max |z| <= 1 + 1e-9
+# on a 21 x 21 k-grid, |U| <= 0.03):
+#   SET_LOW_NU   nu in [0.003, 0.1] for Pr in [0.5, 0.71] (searched at nu 0.003, Pr 0.71);
+#   SET_HIGH_PR  nu in [0.01, 0.35] for Pr in [0.5, 1.0]  (searched at nu 0.005, Pr 1.0).
+# pstar itself is stable for nu >= 0.03 at Pr <= 0.9 and unstable for Pr >= 0.93.
+SET_LOW_NU = (0.5105925173414232, 0.36284305707154935, 0.15375698786144854, 0.19957761259165652,
+              -0.8246361124294435, 0.45127975266252085, 0.042829871476437284, 0.30139798738512336,
+              0.6571556784798335, 0.4287662694105171, 1.4000349991716017)
+SET_HIGH_PR = (0.5380898546127793, 0.16261587889116952, 0.11007573675017865, 0.20438685516974286,
+               -0.9009122586041832, 0.5225617224127665, 0.05449435477260242, 0.4203578356399446,
+               0.7999481655065166, 0.7180603877966116, 1.4786106341856398)
+
+
+def select(nu, Pr):
+    """A free-parameter set that is linearly stable at (nu, Pr) for background
+    speeds up to 0.03, from the sets above; ValueError outside their ranges."""
+    from . import stability
+    if nu >= 0.01 and 0.5 <= Pr <= 1.0:
+        return stability.make_params(SET_HIGH_PR, nu, Pr)
+    if 0.003 <= nu <= 0.1 and 0.5 <= Pr <= 0.71:
+        return stability.make_params(SET_LOW_NU, nu, Pr)
+    raise ValueError(f"no stable parameter set known for nu = {nu}, Pr = {Pr}")
+
+
+def stable_viscosity(nu, Pr):
+    """The smallest viscosity >= nu for which select() has a set."""
+    if 0.5 <= Pr <= 0.71:
+        return max(nu, 0.003)
+    return max(nu, 0.01)

@@ -1,0 +1,211 @@
+"""Continuous-batching solve server for cavity and channel requests.
+
+Requests arrive over time (a seeded Poisson stream).  A request is admitted
+when a slot is free and its lattice fits in the device-memory budget; from then
+on its populations stay on the device and it is stepped together with every
+other admitted request in one batched launch per time step (a plan over the
+active lattices, rebuilt when the set changes).  Every `check_every` steps the
+FP64 residuals of all active lattices are read back in one synchronisation;
+a request retires when its residual reaches its tolerance, freeing its slot and
+memory for the queue.  Admission and retirement happen only between rounds of
+`check_every` steps, so each request sees the same sequence of steps and checks
+whether it runs alone or in a mix: its result does not depend on the mix.
+
+The baseline mode steps each lattice with its own launches in FP64 (the plain
+one-lattice-per-launch path), with the same admission and checks.
+"""
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import lbm13, params as P, workloads as W
+
+
+@dataclass
+class Request:
+    rid: int
+    kind: str          # "cavity" or "channel"
+    L: int             # cavity side, or channel length (height L/4)
+    Ra: float = 1e4    # cavity Rayleigh number
+    Pr: float = 0.71
+    tol: float = 1e-7
+    arrival: float = 0.0   # seconds after the start of the run
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    nx: int
+    ny: int
+    Ra: float
+    Pr: float
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    converged: bool
+    residual: float
+    Nu: float
+    S_u: float
+    S_T: float
+    umax: float
+    rho_total: float
+    tts: float          # time to steady state: finished - arrival (queueing included)
+
+
+def request_setup(req):
+    """(nx, ny, params, boundary) of a request."""
+    if req.kind == "cavity":
+        nu = 0.05 * req.L * math.sqrt(req.Pr / req.Ra)
+        nu = min(P.stable_viscosity(nu, req.Pr), 0.35)
+        p = P.select(nu, req.Pr)
+        T0 = P.rest_temperature(p)
+        kappa = nu / req.Pr
+        g = req.Ra * nu * kappa * T0 / (0.01 * req.L ** 3)
+        return req.L, req.L, p, W.cavity(T0, 0.01, g, rho_ref=1.0, wall_density=1)
+    # Poiseuille channel with temperature walls (Sec. 8): u_max = 0.02 at nu = 0.1
+    ny = max(16, req.L // 4)
+    p = P.select(0.1, req.Pr)
+    T0 = P.rest_temperature(p)
+    g = 8 * 0.1 * 0.02 / ny ** 2
+    return req.L, ny, p, W.poiseuille(g, T0=T0, dT=0.01, wall_density=1)
+
+
+def lattice_bytes(nx, ny, precision):
+    """Device bytes a request holds: two population buffers, wall corrections
+    and the FP64 reduction buffers."""
+    elem = 8 if precision == lbm13.FP64 else 4
+    pitch = (nx + 31) // 32 * 32
+    return 2 * 13 * elem * pitch * ny + elem * (16 * max(nx, ny) + 4) + 8 * (6 * nx * ny + 1216 * 16 + 32)
+
+
+def poisson_trace(n, rate, seed=5151, side_range=(64, 192), ra_range=(1e3, 1e5), Pr=0.71, tol=1e-7):
+    """n requests, exponential inter-arrival times of mean 1/rate, alternating
+    cavity/channel (50/50), side log-uniform in side_range rounded to a
+    multiple of 32, Ra log-uniform in ra_range."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(g.exponential(1.0 / rate, n))
+    out = []
+    for i in range(n):
+        side = int(round(math.exp(g.uniform(math.log(side_range[0]), math.log(side_range[1]))) / 32) * 32)
+        ra = math.exp(g.uniform(math.log(ra_range[0]), math.log(ra_range[1])))
+        kind = "cavity" if i % 2 == 0 else "channel"
+        out.append(Request(i, kind, max(32, side), ra, Pr, tol, float(t[i])))
+    return out
+
+
+@dataclass
+class _Active:
+    req: Request
+    lat: object
+    nx: int
+    ny: int
+    bytes: int
+    admitted: float
+    steps: int = 0
+
+
+class Server:
+    def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
+                 max_steps=2_000_000, batched=True, realtime=True):
+        self.precision = precision
+        self.hbm_budget = hbm_budget
+        self.max_slots = max_slots
+        self.check_every = check_every
+        self.max_steps = max_steps
+        self.batched = batched
+        self.realtime = realtime
+
+    def run(self, requests):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active, results = [], []
+        used = 0
+        plan = None
+        t0 = time.perf_counter()
+        clock_offset = 0.0
+        now = lambda: time.perf_counter() - t0 + clock_offset
+        lattice_steps = 0
+        while pending or active:
+            changed = False
+            while pending and pending[0].arrival <= now() and len(active) < self.max_slots:
+                nx, ny, p, bnd = request_setup(pending[0])
+                b = lattice_bytes(nx, ny, self.precision)
+                if used + b > self.hbm_budget:
+                    if not active:
+                        raise ValueError(f"request {pending[0].rid} needs {b} bytes, above the budget")
+                    break
+                req = pending.pop(0)
+                lat = lbm13.Lattice(nx, ny, p, bnd, precision=self.precision)
+                lat.set_state(1.0, 0.0, 0.0, P.rest_temperature(p))
+                lat.residual()
+                active.append(_Active(req, lat, nx, ny, b, now()))
+                used += b
+                changed = True
+            if not active:
+                wait = pending[0].arrival - now()
+                if wait > 0:
+                    if self.realtime:
+                        time.sleep(wait)
+                    else:
+                        clock_offset += wait
+                continue
+            if self.batched:
+                if changed or plan is None:
+                    if plan is not None:
+                        plan.close()
+                    plan = lbm13.Plan([a.lat for a in active])
+                    plan.set_config(1, 4, 0, 2)
+                plan.step(self.check_every)
+                res = plan.residual(raise_on_divergence=False)
+            else:
+                for a in active:
+                    a.lat.step(self.check_every)
+                res = np.array([a.lat.residual(raise_on_divergence=False) for a in active])
+            lattice_steps += self.check_every * sum(a.nx * a.ny for a in active)
+            keep = []
+            for a, r in zip(active, res):
+                a.steps += self.check_every
+                done = (r[13] > 0 and r[0] <= a.req.tol) or a.steps >= self.max_steps or r[12] > 0
+                if done:
+                    t = now()
+                    results.append(Result(a.req.rid, a.req.kind, a.nx, a.ny, a.req.Ra, a.req.Pr, a.req.arrival,
+                                          a.admitted, t, a.steps, bool(r[13] > 0 and r[0] <= a.req.tol),
+                                          float(r[0]), float(r[8]), float(r[9]), float(r[10]), float(r[11]),
+                                          float(r[4]), t - a.req.arrival))
+                    a.lat.close()
+                    used -= a.bytes
+                    changed = True
+                else:
+                    keep.append(a)
+            if changed and plan is not None:
+                plan.close()
+                plan = None
+            active = keep
+        if plan is not None:
+            plan.close()
+        wall = now()
+        tts = np.array([r.tts for r in results])
+        summary = {"requests": len(results), "converged": int(sum(r.converged for r in results)),
+                   "wall_s": wall, "p50_tts_s": float(np.percentile(tts, 50)), "p99_tts_s": float(np.percentile(tts, 99)),
+                   "throughput_req_s": len(results) / wall, "MLUPS": lattice_steps / wall / 1e6,
+                   "precision": "fp64" if self.precision == lbm13.FP64 else "fp32-deviation",
+                   "batched": self.batched}
+        return sorted(results, key=lambda r: r.rid), summary
+
+
+def batch_workload(n=256, seed=4242, sides=(64, 96, 128, 192, 256, 384, 512), ra_range=(1e3, 1e6),
+                   pr_range=(0.5, 1.0)):
+    """The batched workload: n cavities, side uniform from `sides`, Ra
+    log-uniform, Pr uniform; each with a parameter set that scans stable at its
+    viscosity (raised to the smallest stable one where needed)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        L = int(g.choice(sides))
+        ra = math.exp(g.uniform(math.log(ra_range[0]), math.log(ra_range[1])))
+        pr = float(g.uniform(*pr_range))
+        out.append(Request(i, "cavity", L, ra, pr))
+    return out

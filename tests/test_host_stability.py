@@ -1,0 +1,42 @@
+"""Host-side linear stability module and parameter selection (no GPU): the
+analytic moment-space Jacobian agrees with the oracle's finite-difference one,
+and the parameter sets that `params.select` hands out scan stable over their
+stated (nu, Pr) ranges while pstar is unstable near Pr = 1 (the paper's warning
+that the thermal and viscous modes merge near a critical Prandtl number)."""
+import numpy as np
+import pytest
+
+from paper_1401_0188_gb300 import params, stability
+
+UL = ((0.0, 0.0), (0.03, 0.0), (0.0212, 0.0212))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_1401_0188_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("U", [(0.0, 0.0), (0.02, 0.01)])
+def test_analytic_jacobian_matches_oracle(U):
+    from oracle import oracle as O, linear
+    p = params.pstar(0.05, 0.71)
+    J = stability.collision_jacobian(p, U)
+    Jo, _ = linear.collision_jacobian(O.Lattice(2, 2, p), 1.0, U[0], U[1])
+    assert np.abs(J - Jo).max() < 1e-8
+
+
+@pytest.mark.parametrize("nu,Pr", [(0.01, 0.5), (0.02, 0.8), (0.05, 0.97), (0.2, 1.0), (0.35, 0.9),
+                                   (0.003, 0.6), (0.006, 0.71), (0.08, 0.55)])
+def test_selected_sets_are_stable(nu, Pr):
+    assert stability.max_growth(params.select(nu, Pr), UL, 21) < 1e-9
+
+
+def test_pstar_unstable_near_unit_prandtl():
+    assert stability.max_growth(params.pstar(0.05, 1.0), UL, 21) > 1e-3
+
+
+def test_select_refuses_unknown_region():
+    with pytest.raises(ValueError):
+        params.select(0.004, 0.95)
+    assert params.stable_viscosity(0.004, 0.95) == 0.01
