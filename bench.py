@@ -188,6 +188,21 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def max_over_ranks(x, device, world):
+    """Largest value of x over all ranks (the slowest replica sets the time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank, steps, seconds_max, world):
+    """Whole-job throughput of N independent replicas: all ranks' lattice
+    updates over the slowest rank's time (weak scaling)."""
+    return world * nodes_per_rank * steps / seconds_max / 1e6
+
+
 def time_steps(lat, steps, torch):
     stream = lat.stream
     start = torch.cuda.Event(enable_timing=True)
@@ -315,13 +330,11 @@ def run_ours(args):
         torch.distributed.barrier()
     with Clocks(local) as clk:
         ms = time_steps(lat, args.steps, torch)
-    elapsed = torch.tensor([ms], device=dev)
     if world > 1:
         torch.distributed.barrier()
-        torch.distributed.all_reduce(elapsed, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(elapsed.item())
+    ms_max = max_over_ranks(ms, dev, world)
     per_launch_s = ms / 1e3 / args.steps
-    value = world * n * n * args.steps / (ms_max / 1e3) / 1e6
+    value = aggregate_mlups(n * n, args.steps, ms_max / 1e3, world)
     peak, peak_kind = measured_peaks()
     achieved = bytes_lu * n * n / per_launch_s / 1e9
     tag = f"step_{args.precision}_{n}"
@@ -350,10 +363,7 @@ def run_ours(args):
         lat.step(args.steps)
         lbm13._check(L.lbm13_moments(lat.handle, outp, mask), lat.handle)
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * n * n * args.steps / float(tt.item()) / 1e6, "unit": UNIT,
+        e2e = {"value": aggregate_mlups(n * n, args.steps, max_over_ranks(dt, dev, world), world), "unit": UNIT,
                "h2d_bytes_per_step": 4 * 8 * n * n / args.steps, "d2h_bytes_per_step": 4 * 8 * n * n / args.steps,
                "note": f"per job: upload (rho,ux,uy,T) from pinned host, {args.steps} steps, download the same 4 fields"}
         del host, out

@@ -49,7 +49,8 @@ def rest_temperature(params):
 # stability.make_params for the mapping.  Scanned stable (max |z| <= 1 + 1e-9
 # on a 21 x 21 k-grid, |U| <= 0.03):
 #   SET_LOW_NU   nu in [0.003, 0.1] for Pr in [0.5, 0.71] (searched at nu 0.003, Pr 0.71);
-#   SET_HIGH_PR  nu in [0.01, 0.35] for Pr in [0.5, 1.0]  (searched at nu 0.005, Pr 1.0).
+#   SET_HIGH_PR  nu in [0.01, 0.35] for Pr in [0.5, 1.0]  (searched at nu 0.005, Pr 1.0);
+#   SET_GAP      nu in [0.005, 0.03] for Pr in [0.5, 0.95] (searched at nu 0.004, Pr 0.95).
 # pstar itself is stable for nu >= 0.03 at Pr <= 0.9 and unstable for Pr >= 0.93.
 SET_LOW_NU = (0.5105925173414232, 0.36284305707154935, 0.15375698786144854, 0.19957761259165652,
               -0.8246361124294435, 0.45127975266252085, 0.042829871476437284, 0.30139798738512336,
@@ -57,6 +58,10 @@ SET_LOW_NU = (0.5105925173414232, 0.36284305707154935, 0.15375698786144854, 0.19
 SET_HIGH_PR = (0.5380898546127793, 0.16261587889116952, 0.11007573675017865, 0.20438685516974286,
                -0.9009122586041832, 0.5225617224127665, 0.05449435477260242, 0.4203578356399446,
                0.7999481655065166, 0.7180603877966116, 1.4786106341856398)
+
+SET_GAP = (0.514685701857462, 0.17842478563835837, 0.12038160750190877, 0.20614735400913026,
+           -0.9404624029864772, 0.49908866373015703, 0.05020697851061984, 0.4543578998715883,
+           0.7805796117579609, 0.659693290434811, 1.5179765139129429)
 
 
 def select(nu, Pr):
@@ -67,6 +72,8 @@ def select(nu, Pr):
         return stability.make_params(SET_HIGH_PR, nu, Pr)
     if 0.003 <= nu <= 0.1 and 0.5 <= Pr <= 0.71:
         return stability.make_params(SET_LOW_NU, nu, Pr)
+    if 0.005 <= nu <= 0.03 and 0.5 <= Pr <= 0.95:
+        return stability.make_params(SET_GAP, nu, Pr)
     raise ValueError(f"no stable parameter set known for nu = {nu}, Pr = {Pr}")
 
 
@@ -74,4 +81,6 @@ def stable_viscosity(nu, Pr):
     """The smallest viscosity >= nu for which select() has a set."""
     if 0.5 <= Pr <= 0.71:
         return max(nu, 0.003)
+    if Pr <= 0.95:
+        return max(nu, 0.005)
     return max(nu, 0.01)

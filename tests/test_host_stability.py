@@ -27,7 +27,8 @@ def test_analytic_jacobian_matches_oracle(U):
 
 
 @pytest.mark.parametrize("nu,Pr", [(0.01, 0.5), (0.02, 0.8), (0.05, 0.97), (0.2, 1.0), (0.35, 0.9),
-                                   (0.003, 0.6), (0.006, 0.71), (0.08, 0.55)])
+                                   (0.003, 0.6), (0.006, 0.71), (0.08, 0.55), (0.005, 0.8), (0.007, 0.95),
+                                   (0.006, 0.9)])
 def test_selected_sets_are_stable(nu, Pr):
     assert stability.max_growth(params.select(nu, Pr), UL, 21) < 1e-9
 
@@ -39,4 +40,7 @@ def test_pstar_unstable_near_unit_prandtl():
 def test_select_refuses_unknown_region():
     with pytest.raises(ValueError):
         params.select(0.004, 0.95)
-    assert params.stable_viscosity(0.004, 0.95) == 0.01
+    with pytest.raises(ValueError):
+        params.select(0.006, 0.99)
+    assert params.stable_viscosity(0.004, 0.95) == 0.005
+    assert params.stable_viscosity(0.004, 0.99) == 0.01
