@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--serving-requests", type=int, default=24)
+    ap.add_argument("--batched-count", type=int, default=256)
+    ap.add_argument("--no-sweep", action="store_true")
     return ap.parse_args()
 
 
@@ -221,9 +223,9 @@ def run_batched(args, torch):
     one launch per step by an autotuned plan, FP32-deviation; against the same
     lattices in FP64, each with its own launches."""
     from paper_1401_0188_gb300 import lbm13, serving as S
-    reqs = S.batch_workload()
-    out = {"workload": "256 cavities, side uniform in {64,96,128,192,256,384,512}, Ra log-uniform [1e3,1e6], "
-                       "Pr uniform [0.5,1.0], seed 4242, from rest"}
+    reqs = S.batch_workload(args.batched_count)
+    out = {"workload": f"{args.batched_count} cavities, side uniform in {{64,96,128,192,256,384,512}}, "
+                       "Ra log-uniform [1e3,1e6], Pr uniform [0.5,1.0], seed 4242, from rest"}
 
     def make(prec):
         lats = []
@@ -271,6 +273,31 @@ def run_batched(args, torch):
         torch.cuda.empty_cache()
     out["nodes_per_step"] = nodes
     out["speedup_vs_fp64_per_lattice"] = out["fp32_plan"]["MLUPS"] / out["fp64_per_lattice"]["MLUPS"]
+    return out
+
+
+def run_sweep(args, torch, peak):
+    """The periodic shear wave at 512^2 .. 8192^2 in both precisions: MLUPS and
+    the fraction of the HBM roofline (at 512^2 and 1024^2 the populations fit
+    in the 129 MB L2, so that fraction is not an HBM measurement)."""
+    from paper_1401_0188_gb300 import lbm13, pstar, rest_temperature, workloads as W
+    p = pstar(NU, PR)
+    T0 = rest_temperature(p)
+    out = []
+    for n in (512, 1024, 2048, 4096, 8192):
+        for prec, name, bl in ((lbm13.FP32_DEVIATION, "fp32", 104), (lbm13.FP64, "fp64", 208)):
+            lat = lbm13.Lattice(n, n, p, W.boundary(), precision=prec)
+            ux, uy = W.shear_wave(n, n, 0.01)
+            lat.set_state(1.0, ux, uy, T0)
+            steps = 256 if name == "fp32" else 32
+            lat.step(8)
+            ms = time_steps(lat, steps, torch) / steps
+            mlups = n * n / (ms / 1e3) / 1e6
+            out.append({"n": n, "precision": name, "MLUPS": mlups, "ms_per_step": ms,
+                        "hbm_frac": mlups * 1e6 * bl / 1e9 / peak, "state_MB": 2 * 13 * bl // 26 * n * n / 1e6})
+            lat.close()
+            del lat
+            torch.cuda.empty_cache()
     return out
 
 
@@ -387,6 +414,9 @@ def run_ours(args):
         del lat
         torch.cuda.empty_cache()
 
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(args, torch, peak)
     batched = None
     if not args.no_batched:
         batched = run_batched(args, torch)
@@ -416,6 +446,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp64": fp64,
+            "sweep": sweep,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -189,6 +189,22 @@ void fill_coef(lbm13_t h, Coef<C> &k)
     k.gx = C(h->b.gx);
     k.gy = C(h->b.gy);
     k.rho_ref = C(h->b.rho_ref);
+    // Scalar block: values of the E, eps, varpi polynomials on the shells
+    // (rest, unit axes, diagonals, distance-2 axes); the increment of a
+    // population of shell s is eps_s d_eps + varpi_s d_varpi with
+    // d_eps = l_eps (c_erho rho + c_epsE E - eps), all linear in the shell sums.
+    const double ME[4] = {-28, -15, -2, 24}, Meps[4] = {140, -2, -67, 34}, Mvpi[4] = {-12, 8, -6, 1};
+    const double le = s[2] / kD[2], lv = s[3] / kD[3];
+    for (int sh = 0; sh < 4; ++sh)
+        for (int l = 0; l < 4; ++l)
+            k.B[sh][l] = C(Meps[sh] * le * (D[6] + p.c_epsE * ME[l] - Meps[l]) +
+                           Mvpi[sh] * lv * (p.c_vpi_rho + p.c_vpi_E * ME[l] - Mvpi[l]));
+    // Tensor block: XX = X1 + 4 X9, XXe = -4 X1 + X9 relaxed and mapped back.
+    const double lXX = s[10] / kD[10], lXXe = s[12] / kD[12];
+    k.t1X1 = C(-lXX - 16.0 * lXXe);
+    k.t1X9 = C(-4.0 * lXX + 4.0 * lXXe);
+    k.t9X1 = C(-4.0 * lXX + 4.0 * lXXe);
+    k.t9X9 = C(-16.0 * lXX - lXXe);
 }
 
 template <typename C>

@@ -61,6 +61,13 @@ struct Coef {
     C R10, h2, k2;            // r_eq = j (c2 + h2 rho + k2 E) = j (R10 + h2 drho + k2 dE)
     C l_eps, l_vpi, l_q, l_r, l_XX, l_XY, l_XXe; // s_k / D_k
     C gx, gy, rho_ref;        // F = (rho - rho_ref) g
+    // The relaxation of eps and varpi is linear in the four shell sums
+    // (f0, unit axes, diagonals, distance-2 axes): B[s][l] gives the increment
+    // of every population of shell s per unit of shell sum l.
+    C B[4][4];
+    // XX and XXe relax linearly in X1 = (f1+f3)-(f2+f4) and X9 = (f9+f11)-(f10+f12):
+    // t1 = l_XX XX_eq + t1X1 X1 + t1X9 X9, t9 = 4 l_XX XX_eq + t9X1 X1 + t9X9 X9.
+    C t1X1, t1X9, t9X1, t9X9;
 };
 
 // m = M df (deviation moments).
@@ -139,6 +146,22 @@ LBM13_HD void inverse_add(const Mom<C> &d, C f[Q])
     for (int j = 0; j < Q; ++j) f[j] += g[j];
 }
 
+// 1/x: an FP32 reciprocal as the seed, then Newton's iteration for 1/x,
+// r <- r + r (1 - x r), which squares the relative error each time (two steps
+// take 2^-23 below double rounding).  FP32 uses its own division.
+LBM13_HD double recip(double x)
+{
+#ifdef __CUDA_ARCH__
+    double r = double(1.0f / float(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+#else
+    return 1.0 / x;
+#endif
+}
+LBM13_HD float recip(float x) { return 1.0f / x; }
+
 // One collision in place (deviation form).  Equilibria of Sec. 2, Eq.
 // (d2q13-moments-equil) at j + F/2; the nine non-conserved moments relax as
 // m* = m + s (m_eq - m); j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2)/rho
@@ -146,41 +169,88 @@ LBM13_HD void inverse_add(const Mom<C> &d, C f[Q])
 template <bool Force, typename C>
 LBM13_HD void collide(C f[Q], const Coef<C> &k)
 {
-    Mom<C> m;
-    forward(f, m);
-    const C rho = C(1) + m.rho;
-    const C inv_rho = C(1) / rho;
-    C Fx = C(0), Fy = C(0), jxh = m.jx, jyh = m.jy;
+    // pair sums and differences of opposite links, then shell sums
+    const C a1 = f[1] + f[3], b1 = f[1] - f[3];
+    const C a2 = f[2] + f[4], b2 = f[2] - f[4];
+    const C a5 = f[5] + f[7], b5 = f[5] - f[7];
+    const C a6 = f[6] + f[8], b6 = f[6] - f[8];
+    const C a9 = f[9] + f[11], b9 = f[9] - f[11];
+    const C a10 = f[10] + f[12], b10 = f[10] - f[12];
+    const C S1 = a1 + a2, X1 = a1 - a2;
+    const C S5 = a5 + a6, X5 = a5 - a6;
+    const C S9 = a9 + a10, X9 = a9 - a10;
+    const C dm = b5 - b6, dp = b5 + b6;
+    // conserved and odd moments (deviations)
+    const C drho = f[0] + S1 + S5 + S9;
+    const C dE = C(-28) * f[0] + C(-15) * S1 + C(-2) * S5 + C(24) * S9;
+    const C jx = b1 + dm + C(2) * b9;
+    const C jy = b2 + dp + C(2) * b10;
+    const C qx = C(-2) * b1 - dm + C(2) * b9;
+    const C qy = C(-2) * b2 - dp + C(2) * b10;
+    const C rx = C(4) * b1 + C(-3) * dm + b9;
+    const C ry = C(4) * b2 + C(-3) * dp + b10;
+    const C rho = C(1) + drho;
+    const C inv_rho = recip(rho);
+    C Fx = C(0), Fy = C(0), jxh = jx, jyh = jy;
     if (Force) {
         const C w = rho - k.rho_ref;
         Fx = w * k.gx;
         Fy = w * k.gy;
-        jxh = m.jx + C(0.5) * Fx;
-        jyh = m.jy + C(0.5) * Fy;
+        jxh = jx + C(0.5) * Fx;
+        jyh = jy + C(0.5) * Fy;
     }
-    const C Q1 = k.Q10 + k.h1 * m.rho + k.k1 * m.E;
-    const C R1 = k.R10 + k.h2 * m.rho + k.k2 * m.E;
-    Mom<C> d;
-    d.rho = C(0);
+    const C Q1 = k.Q10 + k.h1 * drho + k.k1 * dE;
+    const C R1 = k.R10 + k.h2 * drho + k.k2 * dE;
+    // scalar block: eps and varpi relax toward c rho + c' E (linear in the shells)
+    C i0 = k.B[0][0] * f[0] + k.B[0][1] * S1 + k.B[0][2] * S5 + k.B[0][3] * S9;
+    C i1 = k.B[1][0] * f[0] + k.B[1][1] * S1 + k.B[1][2] * S5 + k.B[1][3] * S9;
+    C i5 = k.B[2][0] * f[0] + k.B[2][1] * S1 + k.B[2][2] * S5 + k.B[2][3] * S9;
+    C i9 = k.B[3][0] * f[0] + k.B[3][1] * S1 + k.B[3][2] * S5 + k.B[3][3] * S9;
+    C djx = C(0), djy = C(0);
     if (Force) {
-        d.E = C(13.0 / 4004.0) * ((C(2) * m.jx + Fx) * Fx + (C(2) * m.jy + Fy) * Fy) * inv_rho;
-        d.jx = Fx * C(1.0 / 14.0);
-        d.jy = Fy * C(1.0 / 14.0);
-    } else {
-        d.E = C(0);
-        d.jx = C(0);
-        d.jy = C(0);
+        // j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2) / rho
+        const C dEF = C(13.0 / 4004.0) * ((C(2) * jx + Fx) * Fx + (C(2) * jy + Fy) * Fy) * inv_rho;
+        i0 += C(-28) * dEF;
+        i1 += C(-15) * dEF;
+        i5 += C(-2) * dEF;
+        i9 += C(24) * dEF;
+        djx = Fx * C(1.0 / 14.0);
+        djy = Fy * C(1.0 / 14.0);
     }
-    d.eps = k.l_eps * (k.cer * m.rho + k.ceE * m.E - m.eps);
-    d.vpi = k.l_vpi * (k.cwr * m.rho + k.cwE * m.E - m.vpi);
-    d.qx = k.l_q * (jxh * Q1 - m.qx);
-    d.qy = k.l_q * (jyh * Q1 - m.qy);
-    d.rx = k.l_r * (jxh * R1 - m.rx);
-    d.ry = k.l_r * (jyh * R1 - m.ry);
-    d.XX = k.l_XX * ((jxh * jxh - jyh * jyh) * inv_rho - m.XX);
-    d.XY = k.l_XY * (jxh * jyh * inv_rho - m.XY);
-    d.XXe = -k.l_XXe * m.XXe;
-    inverse_add<false>(d, f);
+    // odd block: q and r relax toward j (c + h rho + k E), at j + F/2
+    const C dqx = k.l_q * (jxh * Q1 - qx), dqy = k.l_q * (jyh * Q1 - qy);
+    const C drx = k.l_r * (jxh * R1 - rx), dry = k.l_r * (jyh * R1 - ry);
+    // tensor block: XX, XY toward the momentum flux, XXe toward 0
+    const C XXeq = (jxh * jxh - jyh * jyh) * inv_rho;
+    const C t1 = k.l_XX * XXeq + k.t1X1 * X1 + k.t1X9 * X9;
+    const C t9 = C(4) * k.l_XX * XXeq + k.t9X1 * X1 + k.t9X9 * X9;
+    const C dXY = k.l_XY * (jxh * jyh * inv_rho - X5);
+    // back to populations through the pairs
+    const C o1 = djx + C(-2) * dqx + C(4) * drx;
+    const C o2 = djy + C(-2) * dqy + C(4) * dry;
+    const C sj = djx + djy, dj = djy - djx;
+    const C sq = dqx + dqy, dq = dqx - dqy;
+    const C sr = drx + dry, dr = drx - dry;
+    const C o5 = sj - sq + C(-3) * sr;
+    const C o6 = dj + dq + C(3) * dr;
+    const C o9 = C(2) * (djx + dqx) + drx;
+    const C o10 = C(2) * (djy + dqy) + dry;
+    const C e13 = i1 + t1, e24 = i1 - t1;
+    const C e57 = i5 + dXY, e68 = i5 - dXY;
+    const C e911 = i9 + t9, e1012 = i9 - t9;
+    f[0] += i0;
+    f[1] += e13 + o1;
+    f[3] += e13 - o1;
+    f[2] += e24 + o2;
+    f[4] += e24 - o2;
+    f[5] += e57 + o5;
+    f[7] += e57 - o5;
+    f[6] += e68 + o6;
+    f[8] += e68 - o6;
+    f[9] += e911 + o9;
+    f[11] += e911 - o9;
+    f[10] += e1012 + o10;
+    f[12] += e1012 - o10;
 }
 
 // Deviation of the equilibrium populations from w for the conserved values
@@ -188,7 +258,7 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
 template <typename C>
 LBM13_HD void equilibrium_dev(C drho, C dE, C jx, C jy, const Coef<C> &k, C f[Q])
 {
-    const C inv_rho = C(1) / (C(1) + drho);
+    const C inv_rho = recip(C(1) + drho);
     const C Q1 = k.Q10 + k.h1 * drho + k.k1 * dE;
     const C R1 = k.R10 + k.h2 * drho + k.k2 * dE;
     Mom<C> d;

@@ -273,10 +273,12 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<T, C> a)
 }
 
 // Many lattices in one launch.  The work list holds (lattice, tile) pairs; a
-// tile is 32 columns x (BY R) rows of one lattice.  Blocks stride over the
-// work list (a persistent grid when gridDim.x < ntiles).  The block copies
-// the lattice's arguments for this step's buffer parity into shared memory
-// with 16-byte loads spread over its threads.
+// tile is 32 columns x (BY R) rows of one lattice.  Each block takes a
+// contiguous run of the work list (one tile when the grid has a block per
+// tile; a longer run in a persistent grid), so consecutive tiles of a block
+// mostly belong to one lattice.  The block copies a lattice's arguments for
+// this step's buffer parity into shared memory with 16-byte loads spread over
+// its threads, only when the lattice changes.
 template <typename T, typename C, int R, int BY>
 __global__ void __launch_bounds__(32 * BY) batch_step_kernel(const BatchDesc<T, C> *__restrict__ descs,
                                                             const int2 *__restrict__ work, int ntiles, int parity)
@@ -287,17 +289,23 @@ __global__ void __launch_bounds__(32 * BY) batch_step_kernel(const BatchDesc<T, 
     constexpr int kWords = int(sizeof(StepArgs<T, C>) / 16);
     static_assert(sizeof(StepArgs<T, C>) % 16 == 0, "StepArgs must be a whole number of 16-byte words");
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_end = min(ntiles, (blockIdx.x + 1) * per);
+    int lattice = -1;
+    for (int t = blockIdx.x * per; t < t_end; ++t) {
         const int2 w = work[t];
-        __syncthreads();
-        const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
-        int4 *dst = reinterpret_cast<int4 *>(&sa);
-        for (int i = tid; i < kWords; i += 32 * BY) dst[i] = __ldg(src + i);
-        if (tid == 0) {
-            s_force = descs[w.x].force;
-            s_tiles_x = descs[w.x].tiles_x;
+        if (w.x != lattice) {
+            __syncthreads();
+            const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
+            int4 *dst = reinterpret_cast<int4 *>(&sa);
+            for (int i = tid; i < kWords; i += 32 * BY) dst[i] = __ldg(src + i);
+            if (tid == 0) {
+                s_force = descs[w.x].force;
+                s_tiles_x = descs[w.x].tiles_x;
+            }
+            __syncthreads();
+            lattice = w.x;
         }
-        __syncthreads();
         const int tx = w.y % s_tiles_x, ty = w.y / s_tiles_x;
         const int x = tx * 32 + threadIdx.x, y0 = (ty * BY + threadIdx.y) * R;
         if (s_force)
