@@ -18,6 +18,7 @@
  *   streaming  f_j(x + v_j, t+1) = f*_j(x, t), periodic or through a wall
  *   Sec. 7, Eq. (d2q13-cl-abb)      mixed bounce-back / anti-bounce-back walls.
  *   Sec. 5 and Sec. 8               buoyancy and body force.
+ *   Sec. 9                          uniform volumetric source of energy.
  *   Sec. 10, Table 1 and Fig. 14    Nusselt number and centro-asymmetry read-outs.
  *
  * Readings where the paper is silent, garbled or inconsistent (each one is a
@@ -49,6 +50,11 @@
  *   R16 asymmetry S_u = max |u(i,j) + u(nx-1-i, ny-1-j)|.
  *   R17 residual: r = max(r_u, r_T), r_u = ||u^n - u^{n-K}||_2 / (K max(||u^n - mean u^n||_2, 1e-6 sqrt(N)))
  *      with the velocity u = (ux, uy) taken as one vector field, r_T the same for T.
+ *   R18 energy source (Sec. 9): a uniform source adds q to the internal-energy
+ *      density p = (E + 28 rho)/26 - |j|^2/(2 rho) at every node and step, so
+ *      E* gains 26 q; like the force it is split about the collision: the
+ *      equilibria are taken at E + 13 q and the temperature read-out is
+ *      half-way through the step, T = (p* - q/2) / rho.
  *   corners: a diagonal that crosses two walls at once bounces back with the
  *      mean of the two walls' data.
  *
@@ -79,6 +85,7 @@ typedef struct {
     orc_wall west, east, south, north;
     double gx, gy, rho_ref;
     int wall_density; /* 0: R12 extrapolation; 1: R12' zero net mass flux at temperature walls */
+    double heat;      /* R18: energy source q per node and step, in units of p */
 } orc_boundary;
 
 typedef struct {
@@ -241,20 +248,22 @@ static void to_moments(const orc_lattice *L, const double f[Q], double m[Q])
 
 /* ------------------------------------------------------------- collision */
 
-/* One node: m = M f; equilibria at j + F/2 (R9); relax the nine
- * non-conserved moments; update the conserved ones by the force; f* = M^-1 m*. */
+/* One node: m = M f; equilibria at j + F/2 (R9) and E + 13 q (R18); relax
+ * the nine non-conserved moments; update the conserved ones by the force and
+ * the energy source; f* = M^-1 m*. */
 static void collide(const orc_lattice *L, const double f[Q], double fs[Q])
 {
     double m[Q], meq[Q], ms[Q];
     to_moments(L, f, m);
     double rho = m[K_RHO], E = m[K_E], jx = m[K_JX], jy = m[K_JY];
     double Fx = (rho - L->b.rho_ref) * L->b.gx, Fy = (rho - L->b.rho_ref) * L->b.gy;
-    equilibrium_moments(L, rho, E, jx + 0.5 * Fx, jy + 0.5 * Fy, meq);
+    const double q = L->b.heat;
+    equilibrium_moments(L, rho, E + 13.0 * q, jx + 0.5 * Fx, jy + 0.5 * Fy, meq);
     for (int k = 0; k < Q; ++k) ms[k] = m[k] - L->s[k] * (m[k] - meq[k]);
     ms[K_RHO] = rho;
     ms[K_JX] = jx + Fx;
     ms[K_JY] = jy + Fy;
-    ms[K_E] = E + 13.0 * ((jx + Fx) * (jx + Fx) + (jy + Fy) * (jy + Fy) - jx * jx - jy * jy) / rho;
+    ms[K_E] = E + 13.0 * ((jx + Fx) * (jx + Fx) + (jy + Fy) * (jy + Fy) - jx * jx - jy * jy) / rho + 26.0 * q;
     to_distribution(L, ms, fs);
 }
 
@@ -539,8 +548,9 @@ void orc_moments(const orc_lattice *L, double *out)
 
 /* Macroscopic fields of the stored post-collision state, [4][ny][nx]:
  * rho; u = (j* - F/2)/rho (the momentum half-way through the force step);
- * T = p/rho with p = (E* + 28 rho)/26 - |j*|^2/(2 rho) (R7; the force step
- * changes E by exactly the kinetic energy, so p is the same before and after). */
+ * T = (p - q/2)/rho with p = (E* + 28 rho)/26 - |j*|^2/(2 rho) (R7; the force
+ * step changes E by exactly the kinetic energy, so p is the same before and
+ * after, and the energy source q adds q to p: R18 reads T half-way). */
 void orc_macro(const orc_lattice *L, double *out)
 {
     const size_t plane = (size_t)L->nx * L->ny;
@@ -550,12 +560,52 @@ void orc_macro(const orc_lattice *L, double *out)
         to_moments(L, f, m);
         double rho = m[K_RHO];
         double Fx = (rho - L->b.rho_ref) * L->b.gx, Fy = (rho - L->b.rho_ref) * L->b.gy;
-        double p = (m[K_E] + 28.0 * rho) / 26.0 - (m[K_JX] * m[K_JX] + m[K_JY] * m[K_JY]) / (2.0 * rho);
+        double p = (m[K_E] + 28.0 * rho) / 26.0 - (m[K_JX] * m[K_JX] + m[K_JY] * m[K_JY]) / (2.0 * rho) -
+                   0.5 * L->b.heat;
         out[0 * plane + i] = rho;
         out[1 * plane + i] = (m[K_JX] - 0.5 * Fx) / rho;
         out[2 * plane + i] = (m[K_JY] - 0.5 * Fy) / rho;
         out[3 * plane + i] = p / rho;
     }
+}
+
+/* Aggregates of Sec. 6, Eq. (d2q13-mesure), generalised to a wave vector
+ * k = 2 pi (kx/nx, ky/ny) and its double 2k:
+ *   out[4 f + 2 h + c] = sum over all nodes of F_f(x, y) trig_c((h + 1) k . (x, y)),
+ * trig_0 = cos, trig_1 = sin, for the deviations from the rest state
+ * F = (rho - 1, ux, uy, T - T0, E* - E0, p - T0) with u, T and p read as in
+ * orc_macro.  The phase is reduced exactly: (h+1) k . r = 2 pi m / (nx ny) with
+ * the integer m taken modulo nx ny. */
+void orc_project(const orc_lattice *L, int kx, int ky, double *out)
+{
+    const int nx = L->nx, ny = L->ny;
+    const size_t plane = (size_t)nx * ny;
+    const long long N = (long long)nx * ny;
+    const double T0 = (L->p.E0 + 28.0) / 26.0;
+    double *mac = (double *)malloc(4 * plane * sizeof(double));
+    double *mom = (double *)malloc(Q * plane * sizeof(double));
+    orc_macro(L, mac);
+    orc_moments(L, mom);
+    for (int i = 0; i < 24; ++i) out[i] = 0.0;
+    const long long kxm = ((long long)kx % nx + nx) % nx, kym = ((long long)ky % ny + ny) % ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t i = (size_t)y * nx + x;
+            const double rho = mac[i], T = mac[3 * plane + i];
+            const double F[6] = {rho - 1.0, mac[plane + i], mac[2 * plane + i], T - T0,
+                                 mom[K_E * plane + i] - L->p.E0, rho * T - T0};
+            const long long m = ((kxm * x) % nx * ny + (kym * y) % ny * nx) % N;
+            for (int h = 0; h < 2; ++h) {
+                const double ang = 2.0 * 3.14159265358979323846 * (double)(((h + 1) * m) % N) / (double)N;
+                const double c = cos(ang), sn = sin(ang);
+                for (int f = 0; f < 6; ++f) {
+                    out[4 * f + 2 * h] += F[f] * c;
+                    out[4 * f + 2 * h + 1] += F[f] * sn;
+                }
+            }
+        }
+    free(mac);
+    free(mom);
 }
 
 /* Compensated (Kahan) sum helper. */

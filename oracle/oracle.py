@@ -32,7 +32,8 @@ class _Wall(C.Structure):
 
 class _Boundary(C.Structure):
     _fields_ = [("west", _Wall), ("east", _Wall), ("south", _Wall), ("north", _Wall),
-                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int)]
+                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int),
+                ("heat", C.c_double)]
 
 
 _lib = None
@@ -58,6 +59,7 @@ def lib():
         L.orc_moments.argtypes = [C.c_void_p, dp]
         L.orc_macro.argtypes = [C.c_void_p, dp]
         L.orc_residual.argtypes = [C.c_void_p, dp]
+        L.orc_project.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
         L.orc_collide_node.argtypes = [C.c_void_p, dp, dp]
         L.orc_basis.argtypes = [dp, dp, dp, C.c_int]
         L.orc_velocities.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -94,17 +96,19 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0, heat=0.0):
+    """Sides, body force F = (rho - rho_ref) g, wall density rule (R12 / R12')
+    and the energy source q per node and step (R18, Sec. 9)."""
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density, "heat": heat}
 
 
 def _mk_boundary(b):
     mk = lambda d: _Wall(int(d["kind"]), float(d.get("u_t", 0.0)), float(d.get("T", 0.0)))
     return _Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
                      float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
-                     int(b.get("wall_density", 0)))
+                     int(b.get("wall_density", 0)), float(b.get("heat", 0.0)))
 
 
 class Lattice:
@@ -174,6 +178,13 @@ class Lattice:
         out = np.zeros(16)
         lib().orc_residual(self._h, _dp(out))
         return out
+
+    def project(self, kx, ky=0):
+        """Sec. 6 aggregates: [field][harmonic][cos, sin] for the fields
+        (rho - 1, ux, uy, T - T0, E - E0, p - T0), harmonics k and 2k."""
+        out = np.zeros(24)
+        lib().orc_project(self._h, int(kx), int(ky), _dp(out))
+        return out.reshape(6, 2, 2)
 
     def collide_node(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)

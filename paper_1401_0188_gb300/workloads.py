@@ -44,11 +44,12 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
-    """wall_density: 0 extrapolated density at temperature walls, 1 zero net mass flux."""
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0, heat=0.0):
+    """wall_density: 0 extrapolated density at temperature walls, 1 zero net
+    mass flux; heat: energy source per node and step (Sec. 9)."""
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density, "heat": heat}
 
 
 def cavity(T0, dT, g, rho_ref=1.0, wall_density=0):
@@ -58,6 +59,15 @@ def cavity(T0, dT, g, rho_ref=1.0, wall_density=0):
     return boundary(west=wall(WALL_MIXED, 0.0, T0 + dT / 2), east=wall(WALL_MIXED, 0.0, T0 - dT / 2),
                     south=wall(WALL_BB), north=wall(WALL_BB), gx=0.0, gy=-abs(g), rho_ref=rho_ref,
                     wall_density=wall_density)
+
+
+def heated_slab(T_w, heat, v_w=0.0, wall_density=1):
+    """Adiabatic-wall test (Sec. 9): periodic in y, a velocity+temperature
+    wall on the west (temperature T_w, tangential velocity v_w), an adiabatic
+    bounce-back wall at rest on the east, and a uniform energy source `heat`
+    per node and step.  The steady temperature is the half-parabola with zero
+    slope at the adiabatic wall."""
+    return boundary(west=wall(WALL_MIXED, v_w, T_w), east=wall(WALL_BB), wall_density=wall_density, heat=heat)
 
 
 def couette(T0, U, dT, wall_density=0):

@@ -1,0 +1,224 @@
+"""Pins of the oracle on the periodic wave workloads of Sec. 4-6 and the
+heated slab of Sec. 9, against closed forms derived from the paper's
+equilibria and rates (not from the oracle's own stepping):
+
+- the energy source (reading R18) raises E by exactly 26 q per node and step;
+- Sec. 9: a uniform source between a temperature wall and an adiabatic wall
+  gives the half-parabola T_w + (q T / (rho D h)) (L xi - xi^2 / 2), with
+  D = nu / Pr the diffusivity of the entropy mode and h = A / 52 the enthalpy
+  the equilibrium energy flux carries per unit mass flux (Eq.
+  d2q13-equiv-edp-ordre-1: (39 + 13 c1 + 2 E0) / 26 = A / 26 = 2 h);
+- Sec. 4: a temperature wave at constant pressure relaxes at D k^2 without
+  exciting sound;
+- Sec. 5: buoyancy on that wave drives v_y linearly in time, with the closed
+  form of the forced, damped transverse mode;
+- Sec. 6: the aggregates of Eq. (d2q13-mesure): V~_y decays at nu k^2 and E~
+  changes at the rate the first-order (Chapman-Enskog) energy flux of the
+  scheme gives, -13 sigma_q gamma k^2 V^2 N, which is proportional to
+  nu k^2 V^2 (sigma_q is proportional to nu).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+NTH = max(1, min(8, os.cpu_count() or 1))
+
+
+def _T0(p):
+    return (p["E0"] + 28) / 26
+
+
+def _A(p):
+    return 13 * p["c1"] + 95 + 2 * p["E0"]
+
+
+def _gamma(p):
+    """d/d(V^2) of G = sum_j v_x^2 (|v|^2 - 3) f_eq,j at rho = 1, u = (0, V),
+    T = T0.  G is a moment of f_eq: projecting v_x^2 (|v|^2 - 3) on the basis
+    (alpha_k = <., p_k> / D_k) leaves E, eps and XX (and varpi with weight 0);
+    with E = E0 + 13 V^2, eps_eq = c_erho + c_epsE E, XX_eq = -V^2."""
+    M, D, _ = O.basis()
+    vx, vy = O.velocities()
+    a = M @ (vx ** 2 * (vx ** 2 + vy ** 2 - 3)) / D
+    return 13 * a[1] + 13 * p["c_epsE"] * a[2] + 13 * p["c_vpi_E"] * a[3] - a[10]
+
+
+def _sigma_q(p):
+    """Eq. (d2q13-sigma-qx) with sigma_XX = 104 nu / A (reading R4)."""
+    A = _A(p)
+    B = 114404 + 51051 * p["c1"] - 11492 * p["c_epsE"] + 7854 * p["E0"]
+    return -1309 / 2 * (104 * p["nu"] / A) * A / B
+
+
+def test_energy_source_heats_a_uniform_state_exactly(pstar):
+    """Periodic, uniform rest state, source q: sum E grows by 26 q N per step,
+    rho and j do not move, and the half-step temperature is
+    T0 + q (t - 1/2) at every node (p = rho T with rho = 1)."""
+    q, n, t = 1e-5, 8, 50
+    lat = O.Lattice(n, n, pstar, O.boundary(heat=q))
+    T0 = _T0(pstar)
+    lat.set_equilibrium(1.0, 0.0, 0.0, T0)
+    r0 = lat.residual()
+    lat.step(t)
+    r = lat.residual()
+    N = n * n
+    assert r[7] - r0[7] == pytest.approx(26 * q * N * t, rel=1e-10)
+    assert abs(r[4] - r0[4]) < 1e-12 and abs(r[5]) < 1e-13 and abs(r[6]) < 1e-13
+    T = lat.macro()[3]
+    assert np.abs(T - (T0 + q * (t - 0.5))).max() < 1e-13
+
+
+def _slab(p, nx, v_w, dT=2e-3):
+    """Sec. 9 slab, periodic in y: temperature wall at T0 (zero-flux density,
+    reading R12') on the west moving at v_w, adiabatic wall at rest on the east.
+    The source is set so that the closed form rises by dT."""
+    T0 = _T0(p)
+    D, h = p["nu"] / p["Pr"], _A(p) / 52
+    q = dT * 2 * D * h / (T0 * nx * nx)
+    b = O.boundary(west=O.wall(O.WALL_MIXED, v_w, T0), east=O.wall(O.WALL_BB), wall_density=1, heat=q)
+    lat = O.Lattice(nx, 2, p, b, nthreads=NTH)
+    lat.set_equilibrium(1.0, 0.0, 0.0, T0)
+    lat.step(int(5 * nx * nx / D))
+    return lat, q, D, h
+
+
+def test_heated_slab_is_a_half_parabola(pstar):
+    """Steady state: all the source leaves through the temperature wall (sum E
+    stationary), and T follows the half-parabola with its vertex on the
+    adiabatic wall, to a wall-scheme error of first order in 1/L."""
+    errs = []
+    for nx in (32, 64):
+        lat, q, D, h = _slab(pstar, nx, 0.0)
+        e1 = lat.residual()[7]
+        lat.step(1000)
+        e2 = lat.residual()[7]
+        assert abs(e2 - e1) < 1e-6 * 26 * q * 2 * nx * 1000
+        T0 = _T0(pstar)
+        xi = np.arange(nx) + 0.5
+        exact = T0 + q * T0 / D / h * (nx * xi - xi ** 2 / 2)
+        T = lat.macro()[3][0]
+        errs.append(np.abs(T - exact).max() / (exact.max() - T0))
+        assert T.argmax() >= nx - 2
+    assert errs[0] < 0.025 and errs[1] < 0.6 * errs[0]
+
+
+def test_moving_slab_heating_follows_first_order_energy_flux(pstar):
+    """The west wall moving at v_w = 0.02: v_y is the linear Couette profile,
+    and the shear adds a uniform heating phi nu (v_w / L)^2 to the source, where
+    the first-order energy flux of the scheme gives phi = sigma_q gamma / nu
+    (phi = 1 for a physical gas; this parameter set gives phi = -0.53, i.e. the
+    scheme cools where it should heat)."""
+    nx, v = 32, 0.02
+    lat0, q, D, h = _slab(pstar, nx, 0.0)
+    lat1, _, _, _ = _slab(pstar, nx, v)
+    m0, m1 = lat0.macro(), lat1.macro()
+    xi = np.arange(nx) + 0.5
+    uy = m1[2][0]
+    assert np.abs(uy - v * (1 - xi / nx)).max() < 0.025 * v
+    T0 = _T0(pstar)
+    rise0, rise1 = m0[3][0] - T0, m1[3][0] - T0
+    phi = _sigma_q(pstar) * _gamma(pstar) / pstar["nu"]
+    assert phi == pytest.approx(-0.530, abs=2e-3)
+    extra = pstar["nu"] * (v / nx) ** 2 / q
+    measured = (rise1[nx // 2:].sum() / rise0[nx // 2:].sum() - 1) / extra
+    assert measured == pytest.approx(phi, abs=0.08)
+
+
+def test_thermal_wave_relaxes_at_diffusivity_without_sound(pstar):
+    """Sec. 4: T = T0 + dT cos kx at constant pressure (rho = T0 / T, reading
+    U8): T~ decays at D k^2, D = nu / Pr, and rho~ stays -T~ / T0 (no acoustic
+    oscillation between density and temperature)."""
+    nx, dT = 128, 1e-4
+    T0 = _T0(pstar)
+    x = np.arange(nx)[None, :] * np.ones((2, 1))
+    T = T0 + dT * np.cos(2 * np.pi * x / nx)
+    lat = O.Lattice(nx, 2, pstar, nthreads=NTH)
+    lat.set_equilibrium(T0 / T, 0.0, 0.0, T)
+    lat.step(100)
+    a1 = lat.project(1)
+    lat.step(4000)
+    a2 = lat.project(1)
+    k = 2 * np.pi / nx
+    D = pstar["nu"] / pstar["Pr"]
+    assert np.log(a2[3, 0, 0] / a1[3, 0, 0]) / 4000 == pytest.approx(-D * k * k, rel=5e-3)
+    for a in (a1, a2):
+        assert a[0, 0, 0] / a[3, 0, 0] == pytest.approx(-1 / T0, rel=1e-2)
+
+
+def test_buoyancy_drives_transverse_velocity_linearly(pstar):
+    """Sec. 5, 510 nodes wide, periodic: the temperature wave at constant
+    pressure with F_y = -g (rho - <rho>): V~_y(t) = -g rho~(0)
+    (e^{-D k^2 t} - e^{-nu k^2 t}) / ((nu - D) k^2), linear in t early on, and
+    no horizontal velocity to speak of."""
+    nx, dT, g = 510, 1e-3, 3e-5
+    T0 = _T0(pstar)
+    x = np.arange(nx)[None, :] * np.ones((2, 1))
+    T = T0 + dT * np.cos(2 * np.pi * x / nx)
+    rho = T0 / T
+    lat = O.Lattice(nx, 2, pstar, O.boundary(gy=-g, rho_ref=float(rho.mean())), nthreads=NTH)
+    lat.set_equilibrium(rho, 0.0, 0.0, T)
+    r0 = lat.project(1)[0, 0, 0]
+    k = 2 * np.pi / nx
+    nu, D = pstar["nu"], pstar["nu"] / pstar["Pr"]
+    for t in (2000, 20000):
+        lat.step(t - lat.t)
+        a = lat.project(1)
+        exact = -g * r0 * (np.exp(-D * k * k * t) - np.exp(-nu * k * k * t)) / ((nu - D) * k * k)
+        assert a[2, 0, 0] == pytest.approx(exact, rel=2e-3)
+        m = lat.macro()
+        assert np.abs(m[1]).max() < 5e-3 * np.abs(m[2]).max()
+
+
+@pytest.fixture(scope="module")
+def transverse():
+    """Sec. 6: u_y = V cos kx, rho = 1, T = T0 on 1024 x 2 (K = 1), and the
+    rate of E~ over steps 4..16 (after the non-equilibrium moments have
+    relaxed, well before the sound period at 2k of ~500 steps matters)."""
+    def run(p, V, nx=1024, long=False):
+        T0 = _T0(p)
+        x = np.arange(nx)[None, :] * np.ones((2, 1))
+        lat = O.Lattice(nx, 2, p, nthreads=NTH)
+        lat.set_equilibrium(1.0, 0.0, V * np.cos(2 * np.pi * x / nx), T0)
+        a0 = lat.project(1)
+        lat.step(4)
+        a4 = lat.project(1)
+        lat.step(12)
+        a16 = lat.project(1)
+        if not long:
+            return a0, a4, a16
+        lat.step(1984)
+        return a0, a4, a16, lat.project(1)
+    return run
+
+
+def test_transverse_wave_aggregates(pstar, transverse):
+    nx, N, V = 1024, 2048, 0.02
+    k = 2 * np.pi / nx
+    a0, a4, a16, a2000 = transverse(pstar, V, long=True)
+    assert a0[2, 0, 0] == pytest.approx(V * N / 2, rel=1e-12)
+    assert a0[4, 1, 0] == pytest.approx(13 * V * V / 2 * N / 2, rel=1e-10)
+    # V~_y decays at nu k^2 once the shear stress has built up
+    decay = np.log(a2000[2, 0, 0] / a16[2, 0, 0]) / 1984
+    assert decay == pytest.approx(-pstar["nu"] * k * k, rel=3e-3)
+    rate = (a16[4, 1, 0] - a4[4, 1, 0]) / 12
+    expect = -13 * _sigma_q(pstar) * _gamma(pstar) * k * k * V * V * N
+    assert rate == pytest.approx(expect, rel=0.01)
+    # (a physical gas, sigma_q gamma = nu, would lose E~ at -13 nu k^2 V^2 N;
+    # this parameter set gains it at 0.53 of that rate)
+
+
+def test_transverse_wave_energy_rate_scales_as_nu_k2_V2(pstar, transverse):
+    """E~ rate / (nu k^2 V^2) is the same at nu = 0.05 and 0.1 and at V = 0.01
+    and 0.02 (sigma_q is proportional to nu; gamma does not depend on it)."""
+    nx, V = 1024, 0.02
+    rates = {}
+    for nu, v in ((0.05, V), (0.1, V), (0.05, V / 2)):
+        p = O.pstar(nu=nu, Pr=0.71)
+        _, a4, a16 = transverse(p, v)
+        rates[(nu, v)] = (a16[4, 1, 0] - a4[4, 1, 0]) / 12 / (nu * v * v)
+    base = rates[(0.05, V)]
+    assert rates[(0.1, V)] == pytest.approx(base, rel=0.01)
+    assert rates[(0.05, V / 2)] == pytest.approx(base, rel=0.01)
