@@ -99,14 +99,20 @@ typedef struct {
 #define LBM13_WALL_DENSITY_EXTRAPOLATE 0
 #define LBM13_WALL_DENSITY_ZERO_FLUX 1
 
-/* Sides and body force.  The force per node is F = (rho - rho_ref) (gx, gy):
- * rho_ref = 0 gives the body force rho g of the Poiseuille test (Sec. 8),
- * rho_ref = 1 the buoyancy force proportional to rho - rho_0 of Sec. 5. */
+/* Sides, body force and energy source.  The force per node is
+ * F = (rho - rho_ref) (gx, gy): rho_ref = 0 gives the body force rho g of the
+ * Poiseuille test (Sec. 8), rho_ref = 1 the buoyancy force proportional to
+ * rho - rho_0 of Sec. 5.  `heat` is the uniform volumetric energy source of
+ * the adiabatic-wall test (Sec. 9): every node gains `heat` of internal-energy
+ * density p = (E + 28 rho)/26 - |j|^2/(2 rho) per step (E* += 26 heat), with
+ * the equilibria taken half-way (at E + 13 heat) and T read half-way,
+ * (p* - heat/2)/rho.  Zero for no source; must be finite. */
 typedef struct {
     lbm13_wall west, east, south, north;
     double gx, gy;
     double rho_ref;
     int wall_density;  /* LBM13_WALL_DENSITY_EXTRAPOLATE or LBM13_WALL_DENSITY_ZERO_FLUX */
+    double heat;       /* energy source per node and step, in units of p */
 } lbm13_boundary;
 
 /* Device-memory provider.  alloc returns a device pointer of at least `bytes`
@@ -239,6 +245,24 @@ int lbm13_moments_device(lbm13_t h, double *out, unsigned mask);
  * Returns LBM13_EDIVERGED (after filling out) when a population is not finite.
  * The first call allocates the snapshot and reduction buffers. */
 int lbm13_residual(lbm13_t h, double *out);
+
+/* Fourier aggregates of Sec. 6, Eq. (d2q13-mesure) (V~_y = sum v_y cos kx,
+ * rho~ and E~ at 2k), generalised: for the wave vector
+ * k = 2 pi (kx / nx, ky / ny) (integers, any sign; reduced modulo nx, ny) and
+ * its double 2k,
+ *   out[LBM13_PROJ(f, h, c)] = sum over all nx*ny nodes of F_f trig_c((h+1) k . (x, y)),
+ * h = 0 for k, 1 for 2k; c = 0 cos, 1 sin; (x, y) node indices.  The fields
+ * F_f are deviations from the rest state: rho - 1, ux, uy, T - T0, E - E0,
+ * p - T0, with u, T, p read as by lbm13_moments (half-way through the force
+ * and the source); for a non-zero wave vector this equals the projection of
+ * the field itself.  Sums run in FP64 in a fixed order (deterministic).
+ * out: host, LBM13_PROJ_COUNT doubles.  Synchronises the lattice's stream.
+ * LBM13_EINVAL for NULL; LBM13_ENOMEM if the small partial-sum buffer cannot
+ * be allocated (allocated on the first call, kept until lbm13_destroy). */
+enum { LBM13_P_RHO = 0, LBM13_P_UX = 1, LBM13_P_UY = 2, LBM13_P_T = 3, LBM13_P_E = 4, LBM13_P_P = 5 };
+#define LBM13_PROJ_COUNT 24
+#define LBM13_PROJ(f, h, c) (4 * (f) + 2 * (h) + (c))
+int lbm13_project(lbm13_t h, int kx, int ky, double *out);
 
 /* Time step counter. */
 int64_t lbm13_time(lbm13_t h);

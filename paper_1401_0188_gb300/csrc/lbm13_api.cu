@@ -41,6 +41,9 @@ struct lbm13_lattice {
     // reductions
     void *red_mem = nullptr;
     ReduceBufs rb{};
+    // Fourier projections: partials [proj_blocks][kProj], then kProj results
+    void *proj_mem = nullptr;
+    int proj_blocks = 0;
     double *out_dev = nullptr;
     int have_snap = 0;
     long long snap_t = 0;
@@ -189,6 +192,11 @@ void fill_coef(lbm13_t h, Coef<C> &k)
     k.gx = C(h->b.gx);
     k.gy = C(h->b.gy);
     k.rho_ref = C(h->b.rho_ref);
+    // Energy source q (Sec. 9): equilibria at E + 13 q, so q_eq and r_eq
+    // shift by 13 q k1 and 13 q k2 per unit of j.
+    const double q = h->b.heat;
+    k.Qh = q == 0.0 ? k.Q10 : C(p.c1 + D[2] + D[3] * (p.E0 + 13.0 * q));
+    k.Rh = q == 0.0 ? k.R10 : C(D[5] + D[4] + p.k2 * (p.E0 + 13.0 * q));
     // Scalar block: values of the E, eps, varpi polynomials on the shells
     // (rest, unit axes, diagonals, distance-2 axes); the increment of a
     // population of shell s is eps_s d_eps + varpi_s d_varpi with
@@ -199,6 +207,12 @@ void fill_coef(lbm13_t h, Coef<C> &k)
         for (int l = 0; l < 4; ++l)
             k.B[sh][l] = C(Meps[sh] * le * (D[6] + p.c_epsE * ME[l] - Meps[l]) +
                            Mvpi[sh] * lv * (p.c_vpi_rho + p.c_vpi_E * ME[l] - Mvpi[l]));
+    // Source: E* gains 26 q, eps and varpi relax toward equilibria raised by
+    // 13 q c_epsE and 13 q c_varpiE.
+    for (int sh = 0; sh < 4; ++sh)
+        k.src[sh] = C(q == 0.0 ? 0.0
+                               : ME[sh] * 26.0 * q / kD[1] + Meps[sh] * le * p.c_epsE * 13.0 * q +
+                                     Mvpi[sh] * lv * p.c_vpi_E * 13.0 * q);
     // Tensor block: XX = X1 + 4 X9, XXe = -4 X1 + X9 relaxed and mapped back.
     const double lXX = s[10] / kD[10], lXXe = s[12] / kD[12];
     k.t1X1 = C(-lXX - 16.0 * lXXe);
@@ -240,6 +254,7 @@ ReadArgs<T> read_args(lbm13_t h)
     a.gx = h->b.gx;
     a.gy = h->b.gy;
     a.rho_ref = h->b.rho_ref;
+    a.heat = h->b.heat;
     return a;
 }
 
@@ -400,7 +415,7 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
         return fail(nullptr, LBM13_EINVAL, "precision must be LBM13_FP64 or LBM13_FP32_DEVIATION");
     const lbm13_boundary &b = *boundary;
     if (!check_wall(b.west) || !check_wall(b.east) || !check_wall(b.south) || !check_wall(b.north) ||
-        !finite_all({b.gx, b.gy, b.rho_ref}))
+        !finite_all({b.gx, b.gy, b.rho_ref, b.heat}))
         return fail(nullptr, LBM13_EINVAL, "bad wall kind or non-finite boundary data");
     if (b.wall_density != LBM13_WALL_DENSITY_EXTRAPOLATE && b.wall_density != LBM13_WALL_DENSITY_ZERO_FLUX)
         return fail(nullptr, LBM13_EINVAL, "wall_density must be LBM13_WALL_DENSITY_EXTRAPOLATE or _ZERO_FLUX");
@@ -435,7 +450,7 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
     fill_coef(h, h->kf);
     fill_walls(h, h->wd);
     fill_walls(h, h->wf);
-    h->force = h->b.gx != 0.0 || h->b.gy != 0.0;
+    h->force = h->b.gx != 0.0 || h->b.gy != 0.0 || h->b.heat != 0.0;
     h->elem = precision == LBM13_FP64 ? sizeof(double) : sizeof(float);
     h->pitch = ((long long)nx + 31) / 32 * 32;
     h->plane = (long long)ny * h->pitch;
@@ -487,6 +502,7 @@ void lbm13_destroy(lbm13_t h)
         const long long n = (long long)h->nx * h->ny;
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
     }
+    if (h->proj_mem) dev_free(h, h->proj_mem, size_t(h->proj_blocks + 1) * kProj * sizeof(double));
     delete h;
 }
 
@@ -696,6 +712,27 @@ int lbm13_residual(lbm13_t h, double *out)
     return LBM13_OK;
 }
 
+int lbm13_project(lbm13_t h, int kx, int ky, double *out)
+{
+    if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!h->proj_mem) {
+        const int nb = reduce_blocks(h->nx, h->ny);
+        h->proj_mem = dev_alloc(h, size_t(nb + 1) * kProj * sizeof(double));
+        if (!h->proj_mem) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the projection buffers");
+        h->proj_blocks = nb;
+    }
+    double *partials = static_cast<double *>(h->proj_mem);
+    double *res = partials + size_t(h->proj_blocks) * kProj;
+    cudaError_t e = h->precision == LBM13_FP64
+                        ? launch_project<double>(read_args<double>(h), kx, ky, partials, h->proj_blocks, res, h->stream)
+                        : launch_project<float>(read_args<float>(h), kx, ky, partials, h->proj_blocks, res, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "projection kernel launch");
+    CK(h, cudaMemcpyAsync(out, res, kProj * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM13_OK;
+}
+
 int64_t lbm13_time(lbm13_t h) { return h ? h->t : -1; }
 
 int lbm13_synchronize(lbm13_t h)
@@ -722,6 +759,7 @@ bool lbm13_state_view(const lbm13_lattice *h, lbm13::StateView *v)
     v->gx = h->b.gx;
     v->gy = h->b.gy;
     v->rho_ref = h->b.rho_ref;
+    v->heat = h->b.heat;
     v->stream = h->stream;
     return true;
 }

@@ -71,7 +71,7 @@ __device__ __forceinline__ void node_fields(const ReadArgs<T> &a, long long idx,
     const double w = rho - a.rho_ref;
     o.ux = (d.jx - 0.5 * w * a.gx) / rho;
     o.uy = (d.jy - 0.5 * w * a.gy) / rho;
-    o.p = (o.m[1] + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho);
+    o.p = (o.m[1] + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho) - 0.5 * a.heat;
     o.T = o.p / rho;
 }
 
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kReduceThreads) fields_kernel(const ReadArgs<T
         const double rho = 1.0 + d.rho;
         const double w = rho - a.rho_ref;
         const double ux = (d.jx - 0.5 * w * a.gx) / rho, uy = (d.jy - 0.5 * w * a.gy) / rho;
-        const double p = (a.rest.E0 + d.E + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho);
+        const double p = (a.rest.E0 + d.E + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho) -
+                         0.5 * a.heat;
         const double Tn = p / rho;
         b.fields[i] = ux;
         b.fields[n + i] = uy;
@@ -299,6 +300,83 @@ __global__ void __launch_bounds__(kReduceThreads) finalize2_kernel(ReduceBufs b,
     }
 }
 
+// --------------------------------------------------------- projections
+
+// Deviations of one node from the rest state: rho - 1, ux, uy, T - T0, E - E0,
+// p - T0, with u, T and p read half-way through the force and the source.
+template <typename T>
+__device__ __forceinline__ void node_deviations(const ReadArgs<T> &a, long long idx, double v[6])
+{
+    double f[Q];
+    load_node(a, idx, f);
+    Mom<double> d;
+    forward(f, d);
+    const double rho = 1.0 + d.rho;
+    const double w = rho - a.rho_ref;
+    const double T0 = (a.rest.E0 + 28.0) / 26.0;
+    const double dp = (d.E + 28.0 * d.rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho) - 0.5 * a.heat;
+    v[0] = d.rho;
+    v[1] = (d.jx - 0.5 * w * a.gx) / rho;
+    v[2] = (d.jy - 0.5 * w * a.gy) / rho;
+    v[3] = (dp - T0 * d.rho) / rho;
+    v[4] = d.E;
+    v[5] = dp;
+}
+
+// Per-block partials of the Fourier projections, [block][kProj]:
+// slot 4 f + 2 h + c = sum F_f trig_c(2 pi (h + 1) m / N), m = (kx x ny + ky y nx) mod N
+// (kx, ky already reduced to [0, nx) x [0, ny)).
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) project_kernel(const ReadArgs<T> a, long long kx, long long ky,
+                                                                 double *__restrict__ partials)
+{
+    const long long n = (long long)a.nx * a.ny;
+    double s[kProj];
+#pragma unroll
+    for (int i = 0; i < kProj; ++i) s[i] = 0.0;
+    for (long long i = (long long)blockIdx.x * kReduceThreads + threadIdx.x; i < n;
+         i += (long long)gridDim.x * kReduceThreads) {
+        const int y = int(i / a.nx), x = int(i - (long long)y * a.nx);
+        double v[6];
+        node_deviations(a, (long long)y * a.pitch + x, v);
+        const long long m = ((kx * x) % a.nx * a.ny + (ky * y) % a.ny * a.nx) % n;
+        double c1, s1, c2, s2;
+        sincospi(2.0 * double(m) / double(n), &s1, &c1);
+        sincospi(2.0 * double((2 * m) % n) / double(n), &s2, &c2);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            s[4 * q + 0] += v[q] * c1;
+            s[4 * q + 1] += v[q] * s1;
+            s[4 * q + 2] += v[q] * c2;
+            s[4 * q + 3] += v[q] * s2;
+        }
+    }
+    __shared__ double sh[kReduceThreads / 32][kProj];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kProj; ++i) s[i] = warp_sum(s[i]);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < kProj; ++i) sh[wid][i] = s[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < kProj) {
+        double t = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) t += sh[w][threadIdx.x];
+        partials[(long long)blockIdx.x * kProj + threadIdx.x] = t;
+    }
+}
+
+// out[i] = sum of the partials of slot i in block order.
+__global__ void project_final_kernel(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
+{
+    const int i = threadIdx.x;
+    if (i >= kProj) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[(long long)b * kProj + i];
+    out[i] = t;
+}
+
 } // namespace
 
 template <typename T>
@@ -339,6 +417,16 @@ cudaError_t launch_reduce(const ReadArgs<T> &a, const ReduceBufs &b, const Reduc
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_project(const ReadArgs<T> &a, int kx, int ky, double *partials, int nblocks, double *out_dev,
+                           cudaStream_t s)
+{
+    const long long kxm = ((long long)kx % a.nx + a.nx) % a.nx, kym = ((long long)ky % a.ny + a.ny) % a.ny;
+    project_kernel<T><<<nblocks, kReduceThreads, 0, s>>>(a, kxm, kym, partials);
+    project_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out_dev);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_init<double>(double *, int, int, long long, long long, const Coef<double> &,
                                          const double *, const double *, const double *, const double *,
                                          cudaStream_t);
@@ -351,5 +439,10 @@ template cudaError_t launch_reduce<double>(const ReadArgs<double> &, const Reduc
                                            double *, cudaStream_t);
 template cudaError_t launch_reduce<float>(const ReadArgs<float> &, const ReduceBufs &, const ReduceConf &,
                                           double *, cudaStream_t);
+
+template cudaError_t launch_project<double>(const ReadArgs<double> &, int, int, double *, int, double *,
+                                            cudaStream_t);
+template cudaError_t launch_project<float>(const ReadArgs<float> &, int, int, double *, int, double *,
+                                           cudaStream_t);
 
 } // namespace lbm13

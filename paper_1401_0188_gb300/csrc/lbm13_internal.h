@@ -88,6 +88,7 @@ struct ReadArgs {
     long long pitch, plane;
     Rest rest;
     double gx, gy, rho_ref;
+    double heat;  // energy source q: T is read half-way, (p* - q/2)/rho
 };
 
 // Launchers (return the cudaError_t of the launch).
@@ -140,8 +141,15 @@ struct ReduceConf {
 
 constexpr int kReduceThreads = 256;
 constexpr int kPartials = 16;
+constexpr int kProj = 24;  // Fourier projections: 6 fields x 2 harmonics x (cos, sin)
 
 int reduce_blocks(int nx, int ny);
+
+// Fourier projections of one lattice: project_kernel over nblocks blocks into
+// partials[nblocks][kProj], then out_dev[kProj] in block order.
+template <typename T>
+cudaError_t launch_project(const ReadArgs<T> &a, int kx, int ky, double *partials, int nblocks, double *out_dev,
+                           cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_reduce(const ReadArgs<T> &a, const ReduceBufs &b, const ReduceConf &c, double *out_dev,
@@ -153,7 +161,7 @@ struct StateView {
     const void *f;
     int nx, ny, precision, device;
     long long pitch, plane;
-    double E0, gx, gy, rho_ref;
+    double E0, gx, gy, rho_ref, heat;
     cudaStream_t stream;
 };
 

@@ -61,6 +61,12 @@ struct Coef {
     C R10, h2, k2;            // r_eq = j (c2 + h2 rho + k2 E) = j (R10 + h2 drho + k2 dE)
     C l_eps, l_vpi, l_q, l_r, l_XX, l_XY, l_XXe; // s_k / D_k
     C gx, gy, rho_ref;        // F = (rho - rho_ref) g
+    // Collision only: Q10 and R10 at E0 + 13 q (equilibria half-way through
+    // the energy source q), and the increments of the four shells from the
+    // source (26 q on E, the shifted eps and varpi equilibria); Qh = Q10,
+    // Rh = R10 and src = 0 without a source.
+    C Qh, Rh;
+    C src[4];
     // The relaxation of eps and varpi is linear in the four shell sums
     // (f0, unit axes, diagonals, distance-2 axes): B[s][l] gives the increment
     // of every population of shell s per unit of shell sum l.
@@ -163,9 +169,11 @@ LBM13_HD double recip(double x)
 LBM13_HD float recip(float x) { return 1.0f / x; }
 
 // One collision in place (deviation form).  Equilibria of Sec. 2, Eq.
-// (d2q13-moments-equil) at j + F/2; the nine non-conserved moments relax as
-// m* = m + s (m_eq - m); j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2)/rho
-// (the force's work on the mean flow); rho is unchanged.
+// (d2q13-moments-equil) at j + F/2 and E + 13 q; the nine non-conserved
+// moments relax as m* = m + s (m_eq - m); j* = j + F and
+// E* = E + 13 (|j + F|^2 - |j|^2)/rho + 26 q (the force's work on the mean
+// flow and the energy source q of Sec. 9); rho is unchanged.  Force selects
+// the instantiation that carries the body force and the energy source.
 template <bool Force, typename C>
 LBM13_HD void collide(C f[Q], const Coef<C> &k)
 {
@@ -199,8 +207,8 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
         jxh = jx + C(0.5) * Fx;
         jyh = jy + C(0.5) * Fy;
     }
-    const C Q1 = k.Q10 + k.h1 * drho + k.k1 * dE;
-    const C R1 = k.R10 + k.h2 * drho + k.k2 * dE;
+    const C Q1 = k.Qh + k.h1 * drho + k.k1 * dE;
+    const C R1 = k.Rh + k.h2 * drho + k.k2 * dE;
     // scalar block: eps and varpi relax toward c rho + c' E (linear in the shells)
     C i0 = k.B[0][0] * f[0] + k.B[0][1] * S1 + k.B[0][2] * S5 + k.B[0][3] * S9;
     C i1 = k.B[1][0] * f[0] + k.B[1][1] * S1 + k.B[1][2] * S5 + k.B[1][3] * S9;
@@ -210,10 +218,10 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
     if (Force) {
         // j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2) / rho
         const C dEF = C(13.0 / 4004.0) * ((C(2) * jx + Fx) * Fx + (C(2) * jy + Fy) * Fy) * inv_rho;
-        i0 += C(-28) * dEF;
-        i1 += C(-15) * dEF;
-        i5 += C(-2) * dEF;
-        i9 += C(24) * dEF;
+        i0 += C(-28) * dEF + k.src[0];
+        i1 += C(-15) * dEF + k.src[1];
+        i5 += C(-2) * dEF + k.src[2];
+        i9 += C(24) * dEF + k.src[3];
         djx = Fx * C(1.0 / 14.0);
         djy = Fy * C(1.0 / 14.0);
     }

@@ -50,7 +50,7 @@ __device__ __forceinline__ double wmax(double v)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) totals_kernel(const T *__restrict__ f, int nx, int ny, long long pitch,
                                                          long long plane, double E0, double gx, double gy,
-                                                         double rho_ref, double *partials)
+                                                         double rho_ref, double heat, double *partials)
 {
     const long long n = (long long)nx * ny;
     const double T0 = (E0 + 28.0) / 26.0;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) totals_kernel(const T *__restrict__ 
         const double rho = 1.0 + d.rho;
         const double w = rho - rho_ref;
         const double ux = (d.jx - 0.5 * w * gx) / rho, uy = (d.jy - 0.5 * w * gy) / rho;
-        const double p = (E0 + d.E + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho);
+        const double p = (E0 + d.E + 28.0 * rho) / 26.0 - (d.jx * d.jx + d.jy * d.jy) / (2.0 * rho) - 0.5 * heat;
         s[0] += d.rho;
         s[1] += d.jx;
         s[2] += d.jy;
@@ -191,10 +191,10 @@ extern "C" int lbm13_totals_noalloc(lbm13_t h, double *out)
     const int nblocks = int((n + kNodesPerBlock - 1) / kNodesPerBlock);
     if (v.precision == LBM13_FP64)
         totals_kernel<double><<<nblocks, kThreads, 0, v.stream>>>(static_cast<const double *>(v.f), v.nx, v.ny, v.pitch,
-                                                                   v.plane, v.E0, v.gx, v.gy, v.rho_ref, scratch);
+                                                                   v.plane, v.E0, v.gx, v.gy, v.rho_ref, v.heat, scratch);
     else
         totals_kernel<float><<<nblocks, kThreads, 0, v.stream>>>(static_cast<const float *>(v.f), v.nx, v.ny, v.pitch,
-                                                                  v.plane, v.E0, v.gx, v.gy, v.rho_ref, scratch);
+                                                                  v.plane, v.E0, v.gx, v.gy, v.rho_ref, v.heat, scratch);
     totals_final<<<1, kThreads, 0, v.stream>>>(scratch, nblocks, n, v.E0, out);
     return cudaGetLastError() == cudaSuccess ? LBM13_OK : LBM13_ECUDA;
 }

@@ -35,7 +35,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
-           "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc")
+           "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project")
 
 
 class Lbm13Error(RuntimeError):
@@ -54,7 +54,8 @@ class Wall(C.Structure):
 
 class Boundary(C.Structure):
     _fields_ = [("west", Wall), ("east", Wall), ("south", Wall), ("north", Wall),
-                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int)]
+                ("gx", C.c_double), ("gy", C.c_double), ("rho_ref", C.c_double), ("wall_density", C.c_int),
+                ("heat", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -103,6 +104,7 @@ def lib():
         "lbm13_moments": (C.c_int, [vp, dp, C.c_uint]),
         "lbm13_moments_device": (C.c_int, [vp, vp, C.c_uint]),
         "lbm13_residual": (C.c_int, [vp, dp]),
+        "lbm13_project": (C.c_int, [vp, C.c_int, C.c_int, dp]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
@@ -141,17 +143,18 @@ def wall(kind=PERIODIC, u_t=0.0, T=0.0):
     return {"kind": kind, "u_t": u_t, "T": T}
 
 
-def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0):
+def boundary(west=None, east=None, south=None, north=None, gx=0.0, gy=0.0, rho_ref=0.0, wall_density=0,
+             heat=0.0):
     w = lambda d: d if d is not None else wall()
     return {"west": w(west), "east": w(east), "south": w(south), "north": w(north),
-            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density}
+            "gx": gx, "gy": gy, "rho_ref": rho_ref, "wall_density": wall_density, "heat": heat}
 
 
 def make_boundary(b):
     mk = lambda d: Wall(int(d["kind"]), float(d.get("u_t", 0.0)), float(d.get("T", 0.0)))
     return Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
                     float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
-                    int(b.get("wall_density", 0)))
+                    int(b.get("wall_density", 0)), float(b.get("heat", 0.0)))
 
 
 def lbm13_version():
@@ -328,6 +331,14 @@ class Lattice:
             return out
         _check(st, self._h)
         return out
+
+    def project(self, kx, ky=0):
+        """Fourier aggregates (Sec. 6): [field][harmonic][cos, sin] for the
+        fields (rho - 1, ux, uy, T - T0, E - E0, p - T0), harmonics k and 2k of
+        k = 2 pi (kx/nx, ky/ny); sums over all nodes."""
+        out = np.zeros(24)
+        _check(lib().lbm13_project(self._h, int(kx), int(ky), _dp(out)), self._h)
+        return out.reshape(6, 2, 2)
 
     def synchronize(self):
         _check(lib().lbm13_synchronize(self._h), self._h)

@@ -64,10 +64,30 @@ SET_GAP = (0.514685701857462, 0.17842478563835837, 0.12038160750190877, 0.206147
            0.7805796117579609, 0.659693290434811, 1.5179765139129429)
 
 
-def select(nu, Pr):
+# A set with physical viscous heating: c1 follows E0 through
+# stability.heating_c1, so sigma_q gamma = nu (stability.viscous_heating_factor
+# = 1 for every nu and Pr; pstar gives -0.53 and the sets above 0.88 to 1.18).
+# Searched at nu 0.05, Pr 0.71 with physical_heating; scanned stable for nu in
+# [0.005, 0.35] at Pr in [0.5, 0.71], [0.005, 0.2] at Pr 0.9 and
+# [0.005, 0.05] at Pr 0.95.
+SET_HEAT = (0.501485, 0.176529, 0.121983, 0.211432, -0.955121, 0.508922, 0.051073, 0.454721, 0.783621,
+            0.656364, 1.479079)
+
+
+def _heat_set_stable(nu, Pr):
+    if not (0.5 <= Pr <= 0.95 and nu >= 0.005):
+        return False
+    return nu <= (0.35 if Pr <= 0.71 else 0.2 if Pr <= 0.9 else 0.05)
+
+
+def select(nu, Pr, physical_heating=True):
     """A free-parameter set that is linearly stable at (nu, Pr) for background
-    speeds up to 0.03, from the sets above; ValueError outside their ranges."""
+    speeds up to 0.03; with physical_heating (the default) the SET_HEAT family
+    wherever it is stable, else the sets above; ValueError outside their
+    ranges."""
     from . import stability
+    if physical_heating and _heat_set_stable(nu, Pr):
+        return stability.make_params(SET_HEAT, nu, Pr, physical_heating=True)
     if nu >= 0.01 and 0.5 <= Pr <= 1.0:
         return stability.make_params(SET_HIGH_PR, nu, Pr)
     if 0.003 <= nu <= 0.1 and 0.5 <= Pr <= 0.71:

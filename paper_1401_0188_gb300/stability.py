@@ -90,7 +90,37 @@ def max_growth(params, U_list=((0.0, 0.0),), n=25):
     return worst
 
 
-def make_params(raw, nu, Pr):
+def _heating_moments():
+    """(a, b): the first-order viscous heating of a transverse wave u_y = V cos kx
+    comes from the q-flux of G = sum_j v_x^2 (|v|^2 - 3) f_eq,j, whose V^2
+    coefficient is gamma = a + b c_epsE: projected on the basis, v_x^2 (|v|^2 - 3)
+    has weight alpha_E on E (which carries 13 V^2), alpha_eps on eps (whose
+    equilibrium carries 13 c_epsE V^2) and alpha_XX on XX (equilibrium -V^2)."""
+    x, y = _V[:, 0], _V[:, 1]
+    alpha = _M @ (x * x * (x * x + y * y - 3)) / _D
+    return 13 * alpha[1] - alpha[10], 13 * alpha[2]
+
+
+def viscous_heating_factor(params):
+    """phi = sigma_q gamma / nu: the viscous heating of the scheme relative to a
+    physical gas (phi = 1).  The first-order energy flux of the scheme carries
+    13 sigma_q d_x G; for a shear wave that is the viscous work term when
+    sigma_q gamma = nu.  With sigma_q = -(1309/2) sigma_XX A / B and
+    sigma_XX = 104 nu / A (Eq. d2q13-sigma-qx), phi = -68068 gamma / B."""
+    a, b = _heating_moments()
+    gamma = a + b * params["c_epsE"]
+    B = 114404 + 51051 * params["c1"] - 11492 * params["c_epsE"] + 7854 * params["E0"]
+    return -1309 / 2 * 104 * gamma / B
+
+
+def heating_c1(E0):
+    """c1 that makes phi = 1 for any c_epsE: 68068 b = 11492 makes the c_epsE
+    terms of gamma and B cancel, leaving 114404 + 51051 c1 + 7854 E0 = -68068 a."""
+    a, _ = _heating_moments()
+    return (-68068 * a - 114404 - 7854 * E0) / 51051
+
+
+def make_params(raw, nu, Pr, physical_heating=False):
     """Free parameters from the search vector
     raw = (x0, x1, x2, x3, c1, k2, c_varpiE, s_eps, s_varpi, s_r, s_XXe):
     rest weights proportional to (x0, x1/4 x4, x2/4 x4, x3/4 x4) on the rest,
@@ -101,6 +131,8 @@ def make_params(raw, nu, Pr):
     m0 = _M @ w
     E0, eps0, vpi0 = m0[1], m0[2], m0[3]
     c1, k2, cvE = raw[4], raw[5], raw[6]
+    if physical_heating:
+        c1 = heating_c1(E0)
     A = 13 * c1 + 95 + 2 * E0
     B0 = 114404 + 51051 * c1 + 7854 * E0
     const = 140 + A * B0 / (22984 * Pr) - eps0
@@ -113,15 +145,16 @@ def make_params(raw, nu, Pr):
 PSTAR_RAW = (0.53, 0.196, 0.07, 0.204, -1.0, 0.4, 0.3, 0.6, 1.25, 1.2, 1.0)
 
 
-def search(nu, Pr, U_max=0.03, start=PSTAR_RAW, n=17, maxiter=600, seed_scale=0.05):
+def search(nu, Pr, U_max=0.03, start=PSTAR_RAW, n=17, maxiter=600, seed_scale=0.05, physical_heating=False):
     """Nelder-Mead for a raw vector whose parameter set scans stable (growth
     <= 1e-11) at background speeds 0, U_max along x and along the diagonal.
+    With physical_heating, c1 follows E0 through `heating_c1` (phi = 1).
     Returns (params, growth) of the best point found."""
     from scipy.optimize import minimize
     Ul = ((0.0, 0.0), (U_max, 0.0), (U_max / np.sqrt(2), U_max / np.sqrt(2)))
 
     def objective(raw):
-        p = make_params(raw, nu, Pr)
+        p = make_params(raw, nu, Pr, physical_heating)
         rates = np.array(raw[7:11])
         if (rates <= 0.02).any() or (rates >= 1.98).any():
             return 1.0
@@ -135,5 +168,5 @@ def search(nu, Pr, U_max=0.03, start=PSTAR_RAW, n=17, maxiter=600, seed_scale=0.
     simplex = [x0] + [x0 * (1 + seed_scale * (np.eye(len(x0))[i] * (1 if i % 2 else -1))) for i in range(len(x0))]
     res = minimize(objective, x0, method="Nelder-Mead",
                    options={"initial_simplex": np.array(simplex), "maxiter": maxiter, "xatol": 1e-6, "fatol": 0.0})
-    best = make_params(res.x, nu, Pr)
+    best = make_params(res.x, nu, Pr, physical_heating)
     return best, max_growth(best, Ul, 25), res.x

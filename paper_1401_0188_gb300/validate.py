@@ -2,6 +2,7 @@
 
   python -m paper_1401_0188_gb300.validate cavity  [--L 256] [--Ra 1e3 1e4 1e5] [--tol 1e-8]
   python -m paper_1401_0188_gb300.validate channels [--nx 1024] [--ny 128]
+  python -m paper_1401_0188_gb300.validate waves [--precision both]
 
 `cavity`: the differentially heated cavity of Sec. 10 in FP64 and in
 FP32-deviation storage, each run until the residual reaches `tol`; prints per
@@ -9,6 +10,8 @@ run Nu, the centro-asymmetry S_u, S_T, max |u|, steps and time, then the FP32
 error against FP64 per result.
 `channels`: the Couette flow of Sec. 7 (moving heated upper wall) and the
 Poiseuille flow of Sec. 8 (body force), compared with their closed forms.
+`waves`: the thermal wave (Sec. 4), buoyancy wave (Sec. 5), transverse-wave
+aggregates (Sec. 6) and heated slab (Sec. 9) against their closed forms.
 One JSON object per line.
 """
 import argparse
@@ -76,6 +79,100 @@ def run_channels(nx, ny, steps_factor):
         lat.close()
 
 
+def _row(nx, ny, fn):
+    return fn(np.arange(nx)[None, :] * np.ones((ny, 1)))
+
+
+def run_waves(precisions):
+    """Sec. 4 thermal wave, Sec. 5 buoyancy wave (510 wide), Sec. 6 transverse
+    wave aggregates and the Sec. 9 heated slab, against their closed forms, for
+    pstar (viscous heating factor -0.53) and the physical-heating set."""
+    from . import stability as S
+    sets = {"pstar": P.pstar(0.05, 0.71), "heating": P.select(0.05, 0.71)}
+    for prec in precisions:
+        name = "fp64" if prec == lbm13.FP64 else "fp32-deviation"
+        for sname, p in sets.items():
+            T0 = P.rest_temperature(p)
+            nu, D = p["nu"], p["nu"] / p["Pr"]
+            phi = S.viscous_heating_factor(p)
+            # Sec. 6: u_y = V cos kx on 1024 x 2; E~ rate over steps 4..16
+            nx, V = 1024, 0.02
+            k = 2 * math.pi / nx
+            lat = lbm13.Lattice(nx, 2, p, W.boundary(), precision=prec)
+            lat.set_state(1.0, 0.0, _row(nx, 2, lambda x: V * np.cos(2 * math.pi * x / nx)), T0)
+            lat.step(4)
+            a4 = lat.project(1)
+            lat.step(12)
+            a16 = lat.project(1)
+            lat.step(1984)
+            a2000 = lat.project(1)
+            rate = (a16[4, 1, 0] - a4[4, 1, 0]) / 12
+            N = 2 * nx
+            print(json.dumps({"case": "transverse_wave", "precision": name, "params": sname, "phi": phi,
+                              "E_rate": rate, "E_rate_first_order": -13 * phi * nu * k * k * V * V * N,
+                              "E_rate_physical": -13 * nu * k * k * V * V * N,
+                              "Vy_decay": math.log(a2000[2, 0, 0] / a16[2, 0, 0]) / 1984, "nu_k2": -nu * k * k}),
+                  flush=True)
+            lat.close()
+            # Sec. 4: T = T0 + dT cos kx at constant pressure on 256 x 2
+            nx, dT = 256, 1e-4
+            k = 2 * math.pi / nx
+            Tf = _row(nx, 2, lambda x: T0 + dT * np.cos(2 * math.pi * x / nx))
+            lat = lbm13.Lattice(nx, 2, p, W.boundary(), precision=prec)
+            lat.set_state(T0 / Tf, 0.0, 0.0, Tf)
+            lat.step(200)
+            a1 = lat.project(1)
+            lat.step(8000)
+            a2 = lat.project(1)
+            print(json.dumps({"case": "thermal_wave", "precision": name, "params": sname,
+                              "T_decay": math.log(a2[3, 0, 0] / a1[3, 0, 0]) / 8000, "D_k2": -D * k * k,
+                              "rho_over_T_times_T0": float(a2[0, 0, 0] / a2[3, 0, 0] * T0)}), flush=True)
+            lat.close()
+            # Sec. 5: buoyancy on the temperature wave, 510 wide, periodic
+            nx, dT, g = 510, 1e-3, 3e-5
+            k = 2 * math.pi / nx
+            Tf = _row(nx, 2, lambda x: T0 + dT * np.cos(2 * math.pi * x / nx))
+            rho = T0 / Tf
+            lat = lbm13.Lattice(nx, 2, p, W.boundary(gy=-g, rho_ref=float(rho.mean())), precision=prec)
+            lat.set_state(rho, 0.0, 0.0, Tf)
+            r0 = lat.project(1)[0, 0, 0]
+            out = {"case": "buoyancy_wave", "precision": name, "params": sname, "nx": nx}
+            for t in (2000, 20000, 100000):
+                lat.step(t - lat.t)
+                a = lat.project(1)
+                exact = -g * r0 * (math.exp(-D * k * k * t) - math.exp(-nu * k * k * t)) / ((nu - D) * k * k)
+                m = lat.macro()
+                out[f"Vy_rel_err_t{t}"] = float(a[2, 0, 0] / exact - 1)
+                out[f"ux_over_uy_t{t}"] = float(np.abs(m[1]).max() / np.abs(m[2]).max())
+            print(json.dumps(out), flush=True)
+            lat.close()
+            # Sec. 9: heated slab, temperature wall at T0 (zero-flux density)
+            # moving at v_w, adiabatic wall at rest; steady state
+            for nx in (64, 128, 256):
+                A = 13 * p["c1"] + 95 + 2 * p["E0"]
+                h = A / 52
+                q = 2e-3 * 2 * D * h / (T0 * nx * nx)
+                xi = np.arange(nx) + 0.5
+                exact = T0 + q * T0 / D / h * (nx * xi - xi ** 2 / 2)
+                rises = {}
+                for vw in (0.0, 0.02):
+                    lat = lbm13.Lattice(nx, 4, p, W.heated_slab(T0, q, vw), precision=prec)
+                    lat.set_state(1.0, 0.0, 0.0, T0)
+                    lat.step(int(5 * nx * nx / D))
+                    m = lat.macro()
+                    rises[vw] = m[3].mean(axis=0) - T0
+                    if vw == 0.0:
+                        err = float(np.abs(m[3].mean(axis=0) - exact).max() / (exact.max() - T0))
+                    else:
+                        uy_err = float(np.abs(m[2].mean(axis=0) - vw * (1 - xi / nx)).max() / vw)
+                    lat.close()
+                extra = nu * (0.02 / nx) ** 2 / q
+                phi_m = float((rises[0.02][nx // 2:].sum() / rises[0.0][nx // 2:].sum() - 1) / extra)
+                print(json.dumps({"case": "heated_slab", "precision": name, "params": sname, "nx": nx, "q": q,
+                                  "T_rel_err": err, "uy_rel_err": uy_err, "phi_measured": phi_m, "phi": phi}),
+                      flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -90,13 +187,19 @@ def main(argv=None):
     h.add_argument("--nx", type=int, default=1024)
     h.add_argument("--ny", type=int, default=128)
     h.add_argument("--steps-factor", type=float, default=3.0)
+    w = sub.add_parser("waves")
+    w.add_argument("--precision", choices=["fp64", "fp32", "both"], default="both")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     if a.cmd == "cavity":
         run_cavity(a.L, a.Ra, a.Pr, a.tol, a.check_every, a.max_steps)
-    else:
+    elif a.cmd == "channels":
         run_channels(a.nx, a.ny, a.steps_factor)
+    else:
+        precs = {"fp64": [lbm13.FP64], "fp32": [lbm13.FP32_DEVIATION],
+                 "both": [lbm13.FP64, lbm13.FP32_DEVIATION]}[a.precision]
+        run_waves(precs)
 
 
 if __name__ == "__main__":

@@ -119,6 +119,12 @@ def _cases(T0):
         "all_mixed_zero_flux": (34, 29, W.boundary(west=W.wall(M, -0.01, hot), east=W.wall(M, 0.015, cold),
                                                    south=W.wall(M, 0.02, T0), north=W.wall(M, -0.01, hot),
                                                    gx=1e-5, gy=-2e-5, rho_ref=1.0, wall_density=1)),
+        # uniform energy source (Sec. 9): heated slab with a moving temperature
+        # wall, a forced periodic box and a buoyant cavity with the source
+        "heated_slab": (40, 24, W.heated_slab(T0, 1e-5, 0.02)),
+        "heated_forced_periodic": (45, 50, W.boundary(gx=2e-5, gy=-1e-5, rho_ref=0.0, heat=2e-6)),
+        "heated_cavity": (48, 40, W.boundary(west=W.wall(M, 0.0, hot), east=W.wall(M, 0.0, cold),
+                                             south=W.wall(B), north=W.wall(B), gy=-2e-4, rho_ref=1.0, heat=1e-6)),
     }
 
 
@@ -213,7 +219,7 @@ def test_checkpoint_resume_is_bit_identical(L, pstar):
 FP32_TOL = {"rho": 1e-7, "u": 1e-7, "T": 1e-7}
 
 
-@pytest.mark.parametrize("case", ["shear", "cavity", "couette", "poiseuille", "lid_driven"])
+@pytest.mark.parametrize("case", ["shear", "cavity", "couette", "poiseuille", "lid_driven", "heated_slab"])
 def test_fp32_deviation_within_stated_bounds(L, pstar, case):
     """FP32-deviation storage against the FP64 oracle after 500 steps: rho, u
     and T within the bounds in FP32_TOL (absolute, lattice units)."""

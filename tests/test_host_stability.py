@@ -28,9 +28,23 @@ def test_analytic_jacobian_matches_oracle(U):
 
 @pytest.mark.parametrize("nu,Pr", [(0.01, 0.5), (0.02, 0.8), (0.05, 0.97), (0.2, 1.0), (0.35, 0.9),
                                    (0.003, 0.6), (0.006, 0.71), (0.08, 0.55), (0.005, 0.8), (0.007, 0.95),
-                                   (0.006, 0.9)])
-def test_selected_sets_are_stable(nu, Pr):
-    assert stability.max_growth(params.select(nu, Pr), UL, 21) < 1e-9
+                                   (0.006, 0.9), (0.35, 0.6), (0.15, 0.85), (0.04, 0.93)])
+@pytest.mark.parametrize("physical_heating", [True, False])
+def test_selected_sets_are_stable(nu, Pr, physical_heating):
+    assert stability.max_growth(params.select(nu, Pr, physical_heating), UL, 21) < 1e-9
+
+
+def test_viscous_heating_factor():
+    """phi = sigma_q gamma / nu: -0.53 for pstar, exactly 1 on the heating
+    family (c1 from heating_c1 cancels c_epsE out of phi), and 1 for the sets
+    select hands out inside that family's range."""
+    assert stability.viscous_heating_factor(params.pstar(0.05, 0.71)) == pytest.approx(-0.530182, abs=1e-6)
+    for cE in (-3.0, -1.3, 0.5):
+        p = dict(params.pstar(0.05, 0.71), c_epsE=cE)
+        p["c1"] = stability.heating_c1(p["E0"])
+        assert stability.viscous_heating_factor(p) == pytest.approx(1.0, abs=1e-12)
+    for nu, Pr in ((0.01, 0.6), (0.3, 0.71), (0.1, 0.9), (0.03, 0.95)):
+        assert stability.viscous_heating_factor(params.select(nu, Pr)) == pytest.approx(1.0, abs=1e-12)
 
 
 def test_pstar_unstable_near_unit_prandtl():

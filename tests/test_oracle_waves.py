@@ -222,3 +222,31 @@ def test_transverse_wave_energy_rate_scales_as_nu_k2_V2(pstar, transverse):
     base = rates[(0.05, V)]
     assert rates[(0.1, V)] == pytest.approx(base, rel=0.01)
     assert rates[(0.05, V / 2)] == pytest.approx(base, rel=0.01)
+
+
+# A parameter set on the physical-heating family (c1 tied to E0 so that
+# 114404 + 51051 c1 + 7854 E0 = -68068 (13 alpha_E - alpha_XX), which makes
+# sigma_q gamma = nu for any c_epsE), found by the linear-stability search and
+# written out here as plain numbers.
+HEAT_SET = {"E0": -11.725106754898267, "c1": -1.0136336515842788, "k2": 0.508922, "c_epsE": -1.3438861210676205,
+            "c_vpi_rho": -4.469293961069932, "c_vpi_E": 0.051073, "Pr": 0.71, "nu": 0.05, "s_eps": 0.454721,
+            "s_vpi": 0.783621, "s_r": 0.656364, "s_XXe": 1.479079}
+
+
+def test_physical_heating_set_heats_like_a_gas(transverse):
+    """On that set the first-order energy flux carries the physical viscous
+    work: E~ changes at -13 nu k^2 V^2 N, and the sheared slab heats by
+    nu (v_w / L)^2 on top of the source (phi = 1)."""
+    p = HEAT_SET
+    assert _sigma_q(p) * _gamma(p) / p["nu"] == pytest.approx(1.0, abs=1e-9)
+    nx, N, V = 1024, 2048, 0.02
+    k = 2 * np.pi / nx
+    _, a4, a16 = transverse(p, V)
+    assert (a16[4, 1, 0] - a4[4, 1, 0]) / 12 == pytest.approx(-13 * p["nu"] * k * k * V * V * N, rel=0.01)
+    nx, v = 32, 0.02
+    lat0, q, _, _ = _slab(p, nx, 0.0)
+    lat1, _, _, _ = _slab(p, nx, v)
+    T0 = _T0(p)
+    rise0, rise1 = lat0.macro()[3][0] - T0, lat1.macro()[3][0] - T0
+    measured = (rise1[nx // 2:].sum() / rise0[nx // 2:].sum() - 1) / (p["nu"] * (v / nx) ** 2 / q)
+    assert measured == pytest.approx(1.0, abs=0.08)
