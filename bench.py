@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--serving-requests", type=int, default=24)
     ap.add_argument("--batched-count", type=int, default=256)
+    ap.add_argument("--batched-config", default="",
+                    help="R,BY,ctas_per_sm,order for the batched plan instead of autotuning")
     ap.add_argument("--no-sweep", action="store_true")
     return ap.parse_args()
 
@@ -243,7 +245,10 @@ def run_batched(args, torch):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if name == "fp32_plan":
             plan = lbm13.Plan(lats)
-            best = plan.tune(4)
+            if args.batched_config:
+                plan.set_config(*[int(v) for v in args.batched_config.split(",")])
+            else:
+                plan.tune(4)
             plan.step(8)
             torch.cuda.synchronize()
             e0.record()
