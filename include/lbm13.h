@@ -293,19 +293,22 @@ const char *lbm13_plan_last_error(lbm13_plan_t p);
 int lbm13_plan_step(lbm13_plan_t p, int64_t n);
 
 /* Autotuner: times every candidate (rows per thread R and warps per block BY
- * of the tile, persistent CTAs per SM or one CTA per tile, and the order of
- * the tiles: by lattice, round robin, largest first) over steps_per_candidate
- * real steps each (+1 warm-up), then keeps the fastest.  The steps taken count
- * as simulation steps.  *best_ms_per_step (may be NULL) gets the best time. */
+ * of the tile, row groups per tile 1, 4 or 16, persistent CTAs per SM or one
+ * CTA per tile, and the order of the tiles: by lattice, round robin, largest
+ * first) over steps_per_candidate real steps each (+1 warm-up), then keeps the
+ * fastest.  The steps taken count as simulation steps.  *best_ms_per_step (may
+ * be NULL) gets the best time. */
 int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step);
 
 /* Choose a configuration: (R, BY) in {(1,4), (2,4), (4,4), (2,2), (1,8)},
  * ctas_per_sm 0 (one CTA per tile) .. 64, order 0 by lattice, 1 round robin,
- * 2 largest first. */
-int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order);
+ * 2 largest first, groups 1 .. 64 row groups of BY * R rows per tile (a tile
+ * is 32 columns x groups * BY * R rows).  LBM13_EINVAL outside these. */
+int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
-/* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried by the last tune. */
-int lbm13_plan_config(lbm13_plan_t p, int64_t out[8]);
+/* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried
+ * by the last tune, groups. */
+int lbm13_plan_config(lbm13_plan_t p, int64_t out[9]);
 
 /* FP64 reductions of every lattice of the plan, host out[count * 16] in the
  * layout of lbm13_residual (lattice i at out + 16 i), with a single

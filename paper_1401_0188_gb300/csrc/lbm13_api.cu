@@ -788,7 +788,7 @@ struct lbm13_plan {
     long long nodes = 0;
     std::vector<int> cur0;
     int parity = 0;  // parity of the next launch relative to cur0
-    int R = 2, BY = 4, ctas = 8, order = 0, grid = 0, sms = 0, tried = 0;
+    int R = 2, BY = 4, ctas = 8, order = 0, groups = 1, grid = 0, sms = 0, tried = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     std::string err;
@@ -875,11 +875,13 @@ int plan_upload_descs(lbm13_plan_t p)
     return LBM13_OK;
 }
 
-// Work list for tile rows of BY * R rows, in one of three orders:
-// 0 lattice by lattice, 1 round robin across lattices, 2 largest lattice first.
+// Work list for tiles of 32 columns x groups * BY * R rows, each packed as
+// (tile row << 16) | tile column (both below 2^15 within the lattice limits),
+// in one of three orders: 0 lattice by lattice, 1 round robin across
+// lattices, 2 largest lattice first.
 int plan_build_work(lbm13_plan_t p)
 {
-    const int rows = p->R * p->BY;
+    const int rows = p->R * p->BY * p->groups;
     const size_t L = p->lats.size();
     std::vector<std::vector<int2>> per(L);
     for (size_t i = 0; i < L; ++i) {
@@ -887,7 +889,7 @@ int plan_build_work(lbm13_plan_t p)
         const int tx = (h->nx + 31) / 32, ty = (h->ny + rows - 1) / rows;
         per[i].reserve(size_t(tx) * ty);
         for (int y = 0; y < ty; ++y)
-            for (int x = 0; x < tx; ++x) per[i].push_back(make_int2(int(i), y * tx + x));
+            for (int x = 0; x < tx; ++x) per[i].push_back(make_int2(int(i), (y << 16) | x));
     }
     std::vector<int2> work;
     std::vector<size_t> idx(L);
@@ -928,13 +930,13 @@ cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
         e = launch_batch_walls<double, double>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
         if (e != cudaSuccess) return e;
         return launch_batch<double, double>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
-                                            p->grid, s);
+                                            p->groups, p->grid, s);
     }
     const auto *d = static_cast<const BatchDesc<float, float> *>(p->desc);
     e = launch_batch_walls<float, float>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
     if (e != cudaSuccess) return e;
-    return launch_batch<float, float>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY, p->grid,
-                                      s);
+    return launch_batch<float, float>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
+                                      p->groups, p->grid, s);
 }
 
 // Re-upload the table when a lattice was stepped or reset outside the plan.
@@ -1049,20 +1051,22 @@ void lbm13_plan_destroy(lbm13_plan_t p)
 
 const char *lbm13_plan_last_error(lbm13_plan_t p) { return p ? p->err.c_str() : g_err.c_str(); }
 
-int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order)
+int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups)
 {
     if (!p) return pfail(nullptr, LBM13_EINVAL, "NULL plan");
-    if (!batch_shape_supported(R, BY) || order < 0 || order > 2 || ctas_per_sm < 0 || ctas_per_sm > 64)
-        return pfail(p, LBM13_EINVAL, "unsupported tile shape, order or CTA count");
+    if (!batch_shape_supported(R, BY) || order < 0 || order > 2 || ctas_per_sm < 0 || ctas_per_sm > 64 ||
+        groups < 1 || groups > 64)
+        return pfail(p, LBM13_EINVAL, "unsupported tile shape, order, CTA count or row groups");
     DeviceGuard g(p->device);
     p->R = R;
     p->BY = BY;
     p->ctas = ctas_per_sm;
     p->order = order;
+    p->groups = groups;
     return plan_build_work(p);
 }
 
-int lbm13_plan_config(lbm13_plan_t p, int64_t out[8])
+int lbm13_plan_config(lbm13_plan_t p, int64_t out[9])
 {
     if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");
     out[0] = p->R;
@@ -1073,6 +1077,7 @@ int lbm13_plan_config(lbm13_plan_t p, int64_t out[8])
     out[5] = p->grid;
     out[6] = p->nodes;
     out[7] = p->tried;
+    out[8] = p->groups;
     return LBM13_OK;
 }
 
@@ -1117,30 +1122,34 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
     DeviceGuard g(p->device);
     static const int shapes[][2] = {{1, 4}, {2, 4}, {4, 4}, {2, 2}, {1, 8}};
     static const int ctas[] = {0, 4, 8, 16};
+    static const int groups[] = {1, 4, 16};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return pfail(p, LBM13_ECUDA, "cudaEventCreate");
     double best = 1e300;
-    int bR = p->R, bBY = p->BY, bC = p->ctas, bO = p->order, rc = LBM13_OK;
+    int bR = p->R, bBY = p->BY, bC = p->ctas, bO = p->order, bG = p->groups, rc = LBM13_OK;
     p->tried = 0;
     for (const auto &sh : shapes) {
         for (int c : ctas) {
-            for (int o = 0; o < 3 && rc == LBM13_OK; ++o) {
-                p->R = sh[0];
-                p->BY = sh[1];
-                p->ctas = c;
-                p->order = o;
-                if ((rc = plan_build_work(p)) != LBM13_OK) break;
-                if ((rc = plan_steps(p, 1)) != LBM13_OK) break;  // warm-up
-                cudaEventRecord(e0, p->stream);
-                if ((rc = plan_steps(p, steps_per_candidate)) != LBM13_OK) break;
-                cudaEventRecord(e1, p->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = pfail(p, LBM13_ECUDA, "tuning event"); break; }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const double per = double(ms) / steps_per_candidate;
-                ++p->tried;
-                if (per < best) { best = per; bR = sh[0]; bBY = sh[1]; bC = c; bO = o; }
+            for (int gr : groups) {
+                for (int o = 0; o < 3 && rc == LBM13_OK; ++o) {
+                    p->R = sh[0];
+                    p->BY = sh[1];
+                    p->ctas = c;
+                    p->order = o;
+                    p->groups = gr;
+                    if ((rc = plan_build_work(p)) != LBM13_OK) break;
+                    if ((rc = plan_steps(p, 1)) != LBM13_OK) break;  // warm-up
+                    cudaEventRecord(e0, p->stream);
+                    if ((rc = plan_steps(p, steps_per_candidate)) != LBM13_OK) break;
+                    cudaEventRecord(e1, p->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = pfail(p, LBM13_ECUDA, "tuning event"); break; }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    const double per = double(ms) / steps_per_candidate;
+                    ++p->tried;
+                    if (per < best) { best = per; bR = sh[0]; bBY = sh[1]; bC = c; bO = o; bG = gr; }
+                }
             }
         }
     }
@@ -1151,6 +1160,7 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
     p->BY = bBY;
     p->ctas = bC;
     p->order = bO;
+    p->groups = bG;
     if ((rc = plan_build_work(p)) != LBM13_OK) return rc;
     if (best_ms_per_step) *best_ms_per_step = best;
     return LBM13_OK;

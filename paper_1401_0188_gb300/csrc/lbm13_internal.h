@@ -109,9 +109,11 @@ cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int *lats, in
 // Tile shapes (rows per thread R, warps per block BY) of the batched kernel.
 bool batch_shape_supported(int R, int BY);
 
+// Batched step over a work list of (lattice, (tile row << 16) | tile column),
+// tiles of 32 columns x groups * BY * R rows.
 template <typename T, typename C>
 cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int R, int BY,
-                         int grid, cudaStream_t s);
+                         int groups, int grid, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_init(T *f, int nx, int ny, long long pitch, long long plane, const Coef<double> &k,

@@ -113,7 +113,7 @@ def lib():
         "lbm13_plan_last_error": (C.c_char_p, [vp]),
         "lbm13_plan_step": (C.c_int, [vp, i64]),
         "lbm13_plan_tune": (C.c_int, [vp, C.c_int, dp]),
-        "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
         "lbm13_plan_config": (C.c_int, [vp, C.POINTER(i64)]),
         "lbm13_plan_residual": (C.c_int, [vp, dp]),
     }
@@ -394,8 +394,9 @@ class Plan:
         _pcheck(lib().lbm13_plan_tune(self._h, int(steps_per_candidate), C.byref(best)), self._h)
         return best.value
 
-    def set_config(self, R=2, BY=4, ctas_per_sm=8, order=0):
-        _pcheck(lib().lbm13_plan_set_config(self._h, int(R), int(BY), int(ctas_per_sm), int(order)), self._h)
+    def set_config(self, R=2, BY=4, ctas_per_sm=8, order=0, groups=1):
+        _pcheck(lib().lbm13_plan_set_config(self._h, int(R), int(BY), int(ctas_per_sm), int(order), int(groups)),
+                self._h)
 
     def residual(self, raise_on_divergence=True):
         """(count, 16) FP64 read-outs of every lattice, one synchronisation."""
@@ -407,7 +408,7 @@ class Plan:
         return out
 
     def config(self):
-        out = (C.c_int64 * 8)()
+        out = (C.c_int64 * 9)()
         _pcheck(lib().lbm13_plan_config(self._h, out), self._h)
-        keys = ("R", "BY", "ctas_per_sm", "order", "tiles", "grid", "nodes", "tried")
+        keys = ("R", "BY", "ctas_per_sm", "order", "tiles", "grid", "nodes", "tried", "groups")
         return {k: int(out[i]) for i, k in enumerate(keys)}

@@ -75,12 +75,14 @@ def test_every_configuration_is_bit_identical(L, precision):
     for R, BY in ((1, 4), (2, 4), (4, 4), (2, 2), (1, 8)):
         for ctas in (0, 1, 8):
             for order in (0, 1, 2):
-                plan.set_config(R, BY, ctas, order)
-                c = plan.config()
-                assert (c["R"], c["BY"], c["ctas_per_sm"], c["order"]) == (R, BY, ctas, order)
-                plan.step(3)
-                for g in b:
-                    g.step(3)
+                for groups in (1, 3, 16):
+                    plan.set_config(R, BY, ctas, order, groups)
+                    c = plan.config()
+                    assert (c["R"], c["BY"], c["ctas_per_sm"], c["order"], c["groups"]) == (R, BY, ctas, order,
+                                                                                              groups)
+                    plan.step(3)
+                    for g in b:
+                        g.step(3)
     _same(a, b)
     plan.close()
 
@@ -91,7 +93,7 @@ def test_tune_then_step(L):
     t0 = a[0].t
     best = plan.tune(2)
     c = plan.config()
-    assert best > 0 and c["tried"] == 60
+    assert best > 0 and c["tried"] == 180
     taken = a[0].t - t0
     assert taken == c["tried"] * 3
     plan.step(40)
@@ -126,6 +128,8 @@ def test_plan_rejects_bad_lattice_lists(L):
     plan = L.Plan([x])
     with pytest.raises(L.Lbm13Error):
         plan.set_config(3, 4, 8, 0)
+    with pytest.raises(L.Lbm13Error):
+        plan.set_config(1, 4, 8, 0, 0)
     with pytest.raises(L.Lbm13Error):
         plan.step(-1)
     plan.close()
