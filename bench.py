@@ -119,25 +119,41 @@ class Clocks:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def traffic_record(tag):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def kernel_hash():
+    """Hash of the sources that define the step kernel (its launch, body and
+    arguments): a profile record only applies to the kernel it was taken on."""
     import hashlib
     src = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(src)):
+    for name in ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_step.cu"):
         with open(os.path.join(src, name), "rb") as f:
             h.update(f.read())
-    digest = h.hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    return h.hexdigest()[:16]
+
+
+def profile_record(fname, tag):
+    """The value recorded under `tag` in profiles/<fname> ("tag hash value"
+    lines) if it was taken on the current step-kernel source; else None."""
+    digest = kernel_hash()
     try:
-        for line in open(path):
+        for line in open(os.path.join(ROOT, "profiles", fname)):
             parts = line.split()
             if len(parts) == 3 and parts[0] == tag and parts[1] == digest:
                 return float(parts[2])
     except OSError:
         pass
     return None
+
+
+def traffic_record(tag):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary."""
+    return profile_record("step_kernel_traffic.txt", tag)
+
+
+# FP64 FMA units: the nominal 1.25 TFLOP/s FP64 of a GB300 at its 2070 MHz
+# maximum SM clock is 2 FMA (4 flops) per SM per clock over 152 SMs.
+FP64_FMA_PER_SM_CLK = 2
+SMS = 152
 
 
 def cpu_baseline(steps_target_s=12.0, n=512):
@@ -419,6 +435,18 @@ def run_ours(args):
         fp64 = {"value": n * n / s64 / 1e6, "unit": UNIT, "ms_per_step": 1e3 * s64, "steps": args.fp64_steps,
                 "bytes_per_lu": 208, "hbm_gbs": 208 * n * n / s64 / 1e9,
                 "hbm_frac": 208 * n * n / s64 / 1e9 / peak}
+        # bound by the FP64 pipe: FP64 instructions per node (DADD + DMUL +
+        # DFMA, counted by ncu on this kernel source) against the issue rate
+        ops = profile_record("step_kernel_fp64_ops.txt", "fp64_instr_per_node")
+        mhz = (clk.summary() or {}).get("sm_max_mhz") or 2070.0
+        peak_alu = FP64_FMA_PER_SM_CLK * SMS * mhz * 1e6 / 1e9
+        fp64["roofline"] = {
+            "bound": "alu", "unit": "G FP64 instr/s", "peak": peak_alu,
+            "achieved": None if ops is None else ops * n * n / s64 / 1e9,
+            "frac": None if ops is None else ops * n * n / s64 / 1e9 / peak_alu,
+            "instr_per_node": ops,
+            "peak_basis": f"{FP64_FMA_PER_SM_CLK} FP64 FMA per SM per clock x {SMS} SMs x {mhz:.0f} MHz "
+                          "(nominal 1.25 TFLOP/s at 2070 MHz)"}
         lat.close()
         del lat
         torch.cuda.empty_cache()
