@@ -157,7 +157,7 @@ class Server:
                     if plan is not None:
                         plan.close()
                     plan = lbm13.Plan([a.lat for a in active])
-                    plan.set_config(1, 4, 0, 2, 4)
+                    plan.set_config(1, 4, 0, 2, 1)
                 plan.step(self.check_every)
                 res = plan.residual(raise_on_divergence=False)
             else:
