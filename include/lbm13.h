@@ -198,8 +198,34 @@ int lbm13_set_stream(lbm13_t h, void *stream);
 
 /* Lattice geometry: out[0] nx, out[1] ny, out[2] pitch (elements per row of a
  * population plane), out[3] precision, out[4] bytes per stored population,
- * out[5] device bytes held, out[6] time step counter. */
+ * out[5] device bytes held, out[6] time step counter, out[7] grid size of the
+ * persistent multi-step launch (0 until one was considered, or if impossible). */
 int lbm13_info(lbm13_t h, int64_t out[8]);
+
+/* How lbm13_step runs n >= 2 steps.  Per-step launches (graph-replayed) are
+ * bound by launch latency on small lattices; a persistent launch advances the
+ * lattice by up to 1024 steps in one cooperative launch whose co-resident
+ * blocks separate the phases of each step by grid barriers (results are
+ * bit-identical).  AUTO (default): persistent when both population buffers
+ * take at most 48 MB (they then stay in L2); OFF: never; ON: whenever a
+ * cooperative launch is possible.  Every barrier wait is bounded (1 s); a
+ * timeout leaves the state incomplete and is reported as LBM13_ETIMEOUT by the
+ * next synchronising call (lbm13_synchronize, lbm13_residual, lbm13_moments,
+ * lbm13_project, lbm13_get_raw_state, lbm13_save).  LBM13_EINVAL for another
+ * mode. */
+#define LBM13_PERSISTENT_AUTO 0
+#define LBM13_PERSISTENT_OFF 1
+#define LBM13_PERSISTENT_ON 2
+int lbm13_set_persistent(lbm13_t h, int mode);
+
+/* Self-check of the grid barrier's bounded wait on the current device: a
+ * cooperative launch of `blocks` blocks runs 4 barriers that wait for
+ * blocks + extra_blocks arrivals.  With extra_blocks = 0 every barrier
+ * completes (*timed_out = 0); with extra_blocks > 0 no barrier can, every wait
+ * runs out after timeout_s and *timed_out = 1, and the context stays usable.
+ * blocks in 1..1024 (and co-resident), extra_blocks in 0..1024, timeout_s in
+ * [1e-3, 2]; LBM13_EINVAL outside, LBM13_ECUDA on a CUDA error. */
+int lbm13_barrier_check(int blocks, int extra_blocks, double timeout_s, int *timed_out);
 
 /* Set the state to the equilibrium of the given fields (host arrays [ny][nx];
  * any NULL field takes its rest value: rho 1, u 0, T T0):

@@ -38,6 +38,11 @@ struct lbm13_lattice {
     // CUDA graphs of kGraphSteps steps, one per starting buffer parity
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // persistent multi-step launches: mode (LBM13_PERSISTENT_*), grid barrier
+    // words (count, generation, error), grid size (0: not possible)
+    int persistent = LBM13_PERSISTENT_AUTO;
+    void *sync_mem = nullptr;
+    int multi_grid = -1;
     // reductions
     void *red_mem = nullptr;
     ReduceBufs rb{};
@@ -63,6 +68,8 @@ int fail(lbm13_t h, int code, const std::string &msg)
     return code;
 }
 
+int check_barrier_error(lbm13_t h);
+
 int cuda_fail(lbm13_t h, cudaError_t e, const char *where)
 {
     return fail(h, LBM13_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -72,6 +79,15 @@ int cuda_fail(lbm13_t h, cudaError_t e, const char *where)
     do {                                                         \
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+// Synchronises the lattice's stream and reports a grid-barrier timeout of an
+// earlier persistent launch (LBM13_ETIMEOUT).
+#define SYNC_CHECK(h)                                     \
+    do {                                                  \
+        CK((h), cudaStreamSynchronize((h)->stream));      \
+        const int rc_ = check_barrier_error(h);           \
+        if (rc_ != LBM13_OK) return rc_;                  \
     } while (0)
 
 // Keeps the lattice's device current for the duration of a call.
@@ -299,9 +315,61 @@ cudaError_t build_graph(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C> 
     return e;
 }
 
+// Persistent launches pay off where a step is launch-bound: both population
+// buffers within this many bytes (well inside the 129 MB L2).
+constexpr size_t kPersistentMaxBytes = 48u << 20;
+constexpr long long kPersistentChunk = 1024;  // steps per persistent launch (bounds a launch's duration)
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
+
+GridSync grid_sync(lbm13_t h)
+{
+    unsigned *w = static_cast<unsigned *>(h->sync_mem);
+    return GridSync{w, w + 1, w + 2, kBarrierTimeoutNs};
+}
+
+template <typename T, typename C>
+bool use_persistent(lbm13_t h, long long n)
+{
+    if (h->persistent == LBM13_PERSISTENT_OFF || n < 2) return false;
+    if (h->persistent == LBM13_PERSISTENT_AUTO && 2 * h->state_bytes > kPersistentMaxBytes) return false;
+    if (h->multi_grid < 0) h->multi_grid = multi_grid<T, C>(h->nx, h->ny, h->force);
+    if (h->multi_grid <= 0) return false;
+    if (!h->sync_mem) {
+        h->sync_mem = dev_alloc(h, 64);
+        if (!h->sync_mem) return false;
+        if (cudaMemsetAsync(h->sync_mem, 0, 64, h->stream) != cudaSuccess) return false;
+    }
+    return true;
+}
+
+// Reports (and clears) a grid-barrier timeout of an earlier persistent launch;
+// the caller has synchronised the stream.
+int check_barrier_error(lbm13_t h)
+{
+    if (!h->sync_mem) return LBM13_OK;
+    unsigned err = 0;
+    CK(h, cudaMemcpy(&err, static_cast<unsigned *>(h->sync_mem) + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err == 0) return LBM13_OK;
+    CK(h, cudaMemset(h->sync_mem, 0, 64));
+    return fail(h, LBM13_ETIMEOUT, "a grid barrier of a persistent step launch timed out; the state is incomplete");
+}
+
 template <typename T, typename C>
 int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
 {
+    if (use_persistent<T, C>(h, n)) {
+        const GridSync g = grid_sync(h);
+        while (n > 0) {
+            const int m = int(n < kPersistentChunk ? n : kPersistentChunk);
+            cudaError_t e = launch_multi<T, C>(step_args<T, C>(h, h->cur, k, w), step_args<T, C>(h, h->cur ^ 1, k, w),
+                                               h->force, m, h->multi_grid, g, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "persistent step launch");
+            h->cur ^= m & 1;
+            h->t += m;
+            n -= m;
+        }
+        return LBM13_OK;
+    }
     if (n >= kGraphSteps) {
         if (!h->gexec[h->cur]) {
             cudaError_t e = build_graph<T, C>(h, h->cur, k, w);
@@ -503,6 +571,7 @@ void lbm13_destroy(lbm13_t h)
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
     }
     if (h->proj_mem) dev_free(h, h->proj_mem, size_t(h->proj_blocks + 1) * kProj * sizeof(double));
+    if (h->sync_mem) dev_free(h, h->sync_mem, 64);
     delete h;
 }
 
@@ -523,7 +592,37 @@ int lbm13_info(lbm13_t h, int64_t out[8])
     out[4] = (int64_t)h->elem;
     out[5] = (int64_t)h->bytes_held;
     out[6] = h->t;
-    out[7] = 0;
+    out[7] = h->multi_grid > 0 ? h->multi_grid : 0;
+    return LBM13_OK;
+}
+
+int lbm13_set_persistent(lbm13_t h, int mode)
+{
+    if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
+    if (mode != LBM13_PERSISTENT_AUTO && mode != LBM13_PERSISTENT_OFF && mode != LBM13_PERSISTENT_ON)
+        return fail(h, LBM13_EINVAL, "mode must be LBM13_PERSISTENT_AUTO, _OFF or _ON");
+    h->persistent = mode;
+    return LBM13_OK;
+}
+
+int lbm13_barrier_check(int blocks, int extra_blocks, double timeout_s, int *timed_out)
+{
+    if (!timed_out || blocks < 1 || blocks > 1024 || extra_blocks < 0 || extra_blocks > 1024 ||
+        !(timeout_s >= 1e-3 && timeout_s <= 2.0))
+        return fail(nullptr, LBM13_EINVAL, "blocks in 1..1024, extra_blocks in 0..1024, timeout_s in [1e-3, 2]");
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, 64);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc (barrier words)");
+    unsigned *w = static_cast<unsigned *>(mem);
+    const GridSync g{w, w + 1, w + 2, (unsigned long long)(timeout_s * 1e9)};
+    unsigned err = 0;
+    e = cudaMemset(mem, 0, 64);
+    if (e == cudaSuccess) e = launch_barrier_check(blocks, unsigned(blocks + extra_blocks), 4, g, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&err, w + 2, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "barrier check");
+    *timed_out = err != 0u;
     return LBM13_OK;
 }
 
@@ -601,7 +700,7 @@ int lbm13_get_raw_state(lbm13_t h, double *f, int64_t *step)
     const double *w = h->derived + 22;
     const size_t n = size_t(h->nx) * h->ny;
     std::vector<unsigned char> host(h->state_bytes);
-    CK(h, cudaStreamSynchronize(h->stream));
+    SYNC_CHECK(h);
     CK(h, cudaMemcpy(host.data(), h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToHost));
     for (int j = 0; j < Q; ++j)
         for (int y = 0; y < h->ny; ++y)
@@ -633,7 +732,7 @@ int lbm13_save(lbm13_t h, void *host, size_t bytes)
     int64_t hdr[8] = {0, h->nx, h->ny, h->precision, h->pitch, h->t, 0, 0};
     std::memcpy(hdr, kMagic, 8);
     std::memcpy(p, hdr, 64);
-    CK(h, cudaStreamSynchronize(h->stream));
+    SYNC_CHECK(h);
     CK(h, cudaMemcpy(p + 64, h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToHost));
     return LBM13_OK;
 }
@@ -689,6 +788,7 @@ int lbm13_moments(lbm13_t h, double *out, unsigned mask)
         cudaError_t e = cudaMemcpyAsync(out, stage, bytes, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "moments download");
+        else rc = check_barrier_error(h);
     } else {
         cudaStreamSynchronize(h->stream);
     }
@@ -705,7 +805,7 @@ int lbm13_residual(lbm13_t h, double *out)
     cudaError_t e = launch_residual(h, h->out_dev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction kernel launch");
     CK(h, cudaMemcpyAsync(out, h->out_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    SYNC_CHECK(h);
     h->have_snap = 1;
     h->snap_t = h->t;
     if (out[LBM13_R_NONFINITE] > 0.0) return fail(h, LBM13_EDIVERGED, "non-finite populations in the state");
@@ -729,7 +829,7 @@ int lbm13_project(lbm13_t h, int kx, int ky, double *out)
                         : launch_project<float>(read_args<float>(h), kx, ky, partials, h->proj_blocks, res, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "projection kernel launch");
     CK(h, cudaMemcpyAsync(out, res, kProj * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    SYNC_CHECK(h);
     return LBM13_OK;
 }
 
@@ -739,7 +839,7 @@ int lbm13_synchronize(lbm13_t h)
 {
     if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
     DeviceGuard g(h->device);
-    CK(h, cudaStreamSynchronize(h->stream));
+    SYNC_CHECK(h);
     return LBM13_OK;
 }
 

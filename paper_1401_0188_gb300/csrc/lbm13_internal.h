@@ -75,6 +75,27 @@ struct BatchDesc {
     int tiles_x;  // ceil(nx / 32)
 };
 
+// Grid barrier words of a persistent launch (device memory, zeroed before use)
+// and the bound on every wait.
+struct GridSync {
+    unsigned *count;   // arrivals at the current barrier
+    unsigned *gen;     // barrier generation
+    unsigned *error;   // nonzero once a wait ran out
+    unsigned long long timeout_ns;
+};
+
+// Persistent multi-step launch of one lattice (lbm13_multi.cu): the largest
+// co-resident grid for its tiles (0 when cooperative launch is unavailable),
+// and nsteps steps alternating a0 (current parity) and a1 in one launch.
+template <typename T, typename C>
+int multi_grid(int nx, int ny, bool force);
+template <typename T, typename C>
+cudaError_t launch_multi(const StepArgs<T, C> &a0, const StepArgs<T, C> &a1, bool force, int nsteps, int grid,
+                         const GridSync &g, cudaStream_t s);
+// `rounds` grid barriers over `grid` blocks that wait for expect_blocks
+// arrivals (expect_blocks > grid makes every wait run out).
+cudaError_t launch_barrier_check(int grid, unsigned expect_blocks, int rounds, const GridSync &g, cudaStream_t s);
+
 // Rest moments used by the read-outs (double precision).
 struct Rest {
     double E0, eps0, vpi0;

@@ -20,6 +20,7 @@ PARAM_FIELDS = ("E0", "c1", "k2", "c_epsE", "c_vpi_rho", "c_vpi_E", "Pr", "nu",
 PERIODIC, WALL_BB, WALL_MIXED = 0, 1, 2
 FP64, FP32_DEVIATION = 0, 1
 WALL_DENSITY_EXTRAPOLATE, WALL_DENSITY_ZERO_FLUX = 0, 1
+PERSISTENT_AUTO, PERSISTENT_OFF, PERSISTENT_ON = 0, 1, 2
 DERIVED_COUNT = 48
 
 FIELD_UX, FIELD_UY, FIELD_T, FIELD_P, FIELD_E_SEC7 = 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17
@@ -35,7 +36,8 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_restore", "lbm13_step", "lbm13_moments", "lbm13_moments_device",
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
-           "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project")
+           "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
+           "lbm13_set_persistent", "lbm13_barrier_check")
 
 
 class Lbm13Error(RuntimeError):
@@ -105,6 +107,8 @@ def lib():
         "lbm13_moments_device": (C.c_int, [vp, vp, C.c_uint]),
         "lbm13_residual": (C.c_int, [vp, dp]),
         "lbm13_project": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "lbm13_set_persistent": (C.c_int, [vp, C.c_int]),
+        "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
@@ -155,6 +159,14 @@ def make_boundary(b):
     return Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
                     float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
                     int(b.get("wall_density", 0)), float(b.get("heat", 0.0)))
+
+
+def barrier_check(blocks, extra_blocks, timeout_s):
+    """Self-check of the grid barrier's bounded wait: True when the waits ran
+    out (expected exactly when extra_blocks > 0)."""
+    out = C.c_int(0)
+    _check(lib().lbm13_barrier_check(int(blocks), int(extra_blocks), float(timeout_s), C.byref(out)))
+    return bool(out.value)
 
 
 def lbm13_version():
@@ -250,7 +262,7 @@ class Lattice:
     def info(self):
         out = (C.c_int64 * 8)()
         _check(lib().lbm13_info(self._h, out), self._h)
-        keys = ("nx", "ny", "pitch", "precision", "elem_bytes", "device_bytes", "step")
+        keys = ("nx", "ny", "pitch", "precision", "elem_bytes", "device_bytes", "step", "persistent_grid")
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     @property
@@ -331,6 +343,11 @@ class Lattice:
             return out
         _check(st, self._h)
         return out
+
+    def set_persistent(self, mode):
+        """PERSISTENT_AUTO (default), PERSISTENT_OFF or PERSISTENT_ON: whether
+        step(n) runs many steps per cooperative launch."""
+        _check(lib().lbm13_set_persistent(self._h, int(mode)), self._h)
 
     def project(self, kx, ky=0):
         """Fourier aggregates (Sec. 6): [field][harmonic][cos, sin] for the
