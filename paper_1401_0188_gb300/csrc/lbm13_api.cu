@@ -324,7 +324,7 @@ constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 GridSync grid_sync(lbm13_t h)
 {
     unsigned *w = static_cast<unsigned *>(h->sync_mem);
-    return GridSync{w, w + 1, w + 2, kBarrierTimeoutNs};
+    return GridSync{w, w + 32, w + 64, kBarrierTimeoutNs};
 }
 
 template <typename T, typename C>
@@ -335,9 +335,9 @@ bool use_persistent(lbm13_t h, long long n)
     if (h->multi_grid < 0) h->multi_grid = multi_grid<T, C>(h->nx, h->ny, h->force);
     if (h->multi_grid <= 0) return false;
     if (!h->sync_mem) {
-        h->sync_mem = dev_alloc(h, 64);
+        h->sync_mem = dev_alloc(h, kSyncBytes);
         if (!h->sync_mem) return false;
-        if (cudaMemsetAsync(h->sync_mem, 0, 64, h->stream) != cudaSuccess) return false;
+        if (cudaMemsetAsync(h->sync_mem, 0, kSyncBytes, h->stream) != cudaSuccess) return false;
     }
     return true;
 }
@@ -348,9 +348,9 @@ int check_barrier_error(lbm13_t h)
 {
     if (!h->sync_mem) return LBM13_OK;
     unsigned err = 0;
-    CK(h, cudaMemcpy(&err, static_cast<unsigned *>(h->sync_mem) + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(&err, static_cast<unsigned *>(h->sync_mem) + 64, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (err == 0) return LBM13_OK;
-    CK(h, cudaMemset(h->sync_mem, 0, 64));
+    CK(h, cudaMemset(h->sync_mem, 0, kSyncBytes));
     return fail(h, LBM13_ETIMEOUT, "a grid barrier of a persistent step launch timed out; the state is incomplete");
 }
 
@@ -571,7 +571,7 @@ void lbm13_destroy(lbm13_t h)
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
     }
     if (h->proj_mem) dev_free(h, h->proj_mem, size_t(h->proj_blocks + 1) * kProj * sizeof(double));
-    if (h->sync_mem) dev_free(h, h->sync_mem, 64);
+    if (h->sync_mem) dev_free(h, h->sync_mem, kSyncBytes);
     delete h;
 }
 
@@ -611,15 +611,15 @@ int lbm13_barrier_check(int blocks, int extra_blocks, double timeout_s, int *tim
         !(timeout_s >= 1e-3 && timeout_s <= 2.0))
         return fail(nullptr, LBM13_EINVAL, "blocks in 1..1024, extra_blocks in 0..1024, timeout_s in [1e-3, 2]");
     void *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, 64);
+    cudaError_t e = cudaMalloc(&mem, kSyncBytes);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc (barrier words)");
     unsigned *w = static_cast<unsigned *>(mem);
-    const GridSync g{w, w + 1, w + 2, (unsigned long long)(timeout_s * 1e9)};
+    const GridSync g{w, w + 32, w + 64, (unsigned long long)(timeout_s * 1e9)};
     unsigned err = 0;
-    e = cudaMemset(mem, 0, 64);
+    e = cudaMemset(mem, 0, kSyncBytes);
     if (e == cudaSuccess) e = launch_barrier_check(blocks, unsigned(blocks + extra_blocks), 4, g, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&err, w + 2, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, w + 64, sizeof(unsigned), cudaMemcpyDeviceToHost);
     cudaFree(mem);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "barrier check");
     *timed_out = err != 0u;

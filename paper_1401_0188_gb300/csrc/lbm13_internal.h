@@ -75,8 +75,9 @@ struct BatchDesc {
     int tiles_x;  // ceil(nx / 32)
 };
 
-// Grid barrier words of a persistent launch (device memory, zeroed before use)
-// and the bound on every wait.
+// Grid barrier words of a persistent launch (device memory, zeroed before use,
+// each on its own 128-byte line: kSyncBytes in all) and the bound on every wait.
+constexpr int kSyncBytes = 512;
 struct GridSync {
     unsigned *count;   // arrivals at the current barrier
     unsigned *gen;     // barrier generation

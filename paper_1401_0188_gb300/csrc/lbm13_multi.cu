@@ -57,13 +57,16 @@ __device__ bool grid_barrier(const GridSync &g, unsigned nblocks)
             atomicAdd(g.gen, 1u);
         } else {
             const unsigned long long t0 = global_ns();
+            unsigned it = 0;
             while (load_acquire(g.gen) == gen) {
-                if (load_acquire(g.error) != 0u) break;
-                if (global_ns() - t0 > g.timeout_ns) {
-                    atomicExch(g.error, 1u);
-                    break;
+                if ((++it & 15u) == 0u) {
+                    if (load_acquire(g.error) != 0u) break;
+                    if (global_ns() - t0 > g.timeout_ns) {
+                        atomicExch(g.error, 1u);
+                        break;
+                    }
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -73,8 +76,9 @@ __device__ bool grid_barrier(const GridSync &g, unsigned nblocks)
 }
 
 // One step of the lattice over the whole grid; false if a barrier timed out.
+// The last step of a launch needs no closing barrier (the launch's end is one).
 template <typename T, typename C, bool Force, int R>
-__device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, int ntiles, C *slot,
+__device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, int ntiles, bool last,
                                           const GridSync &g)
 {
     if (a.any_wall_data) {
@@ -85,9 +89,9 @@ __device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, 
     }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x, ty = t / tiles_x;
-        process_column<T, C, Force, R>(a, tx * 32 + threadIdx.x, (ty * 4 + threadIdx.y) * R, slot);
+        process_column<T, C, Force, R>(a, tx * 32 + threadIdx.x, (ty * 4 + threadIdx.y) * R);
     }
-    return grid_barrier(g, gridDim.x);
+    return last || grid_barrier(g, gridDim.x);
 }
 
 // nsteps steps alternating a0 (the current buffer parity) and a1.
@@ -95,13 +99,11 @@ template <typename T, typename C, bool Force, int R>
 __global__ void __launch_bounds__(128) multi_step_kernel(const StepArgs<T, C> a0, const StepArgs<T, C> a1,
                                                          int nsteps, const GridSync g)
 {
-    __shared__ C slots[128][Q];
-    C *slot = slots[threadIdx.y * 32 + threadIdx.x];
     const int tiles_x = (a0.nx + 31) / 32;
     const int ntiles = tiles_x * ((a0.ny + 4 * R - 1) / (4 * R));
     for (int s = 0; s < nsteps; s += 2) {
-        if (!grid_step<T, C, Force, R>(a0, tiles_x, ntiles, slot, g)) return;
-        if (s + 1 < nsteps && !grid_step<T, C, Force, R>(a1, tiles_x, ntiles, slot, g)) return;
+        if (!grid_step<T, C, Force, R>(a0, tiles_x, ntiles, s + 1 >= nsteps, g)) return;
+        if (s + 1 < nsteps && !grid_step<T, C, Force, R>(a1, tiles_x, ntiles, s + 2 >= nsteps, g)) return;
     }
 }
 
