@@ -125,7 +125,7 @@ def kernel_hash():
     import hashlib
     src = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_step.cu"):
+    for name in ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_stepdev.cuh", "lbm13_step.cu"):
         with open(os.path.join(src, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -202,17 +202,16 @@ int lbm13_set_stream(lbm13_t h, void *stream);
  * persistent multi-step launch (0 until one was considered, or if impossible). */
 int lbm13_info(lbm13_t h, int64_t out[8]);
 
-/* How lbm13_step runs n >= 2 steps.  Per-step launches (graph-replayed) are
- * bound by launch latency on small lattices; a persistent launch advances the
- * lattice by up to 1024 steps in one cooperative launch whose co-resident
- * blocks separate the phases of each step by grid barriers (results are
- * bit-identical).  AUTO (default): persistent when both population buffers
- * take at most 48 MB (they then stay in L2); OFF: never; ON: whenever a
- * cooperative launch is possible.  Every barrier wait is bounded (1 s); a
- * timeout leaves the state incomplete and is reported as LBM13_ETIMEOUT by the
- * next synchronising call (lbm13_synchronize, lbm13_residual, lbm13_moments,
- * lbm13_project, lbm13_get_raw_state, lbm13_save).  LBM13_EINVAL for another
- * mode. */
+/* How lbm13_step runs n >= 2 steps: per-step launches (replayed from CUDA
+ * graphs in runs of 32), or a persistent launch that advances the lattice by
+ * up to 1024 steps in one cooperative launch whose co-resident blocks separate
+ * the phases of each step by grid barriers (results are bit-identical).
+ * AUTO (default) and OFF: per-step launches (on GB300 they are faster at every
+ * size measured, 64^2 to 512^2); ON: persistent whenever a cooperative launch
+ * is possible.  Every barrier wait is bounded (1 s); a timeout leaves the
+ * state incomplete and is reported as LBM13_ETIMEOUT by the next synchronising
+ * call (lbm13_synchronize, lbm13_residual, lbm13_moments, lbm13_project,
+ * lbm13_get_raw_state, lbm13_save).  LBM13_EINVAL for another mode. */
 #define LBM13_PERSISTENT_AUTO 0
 #define LBM13_PERSISTENT_OFF 1
 #define LBM13_PERSISTENT_ON 2

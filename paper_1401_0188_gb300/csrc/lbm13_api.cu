@@ -315,9 +315,6 @@ cudaError_t build_graph(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C> 
     return e;
 }
 
-// Persistent launches pay off where a step is launch-bound: both population
-// buffers within this many bytes (well inside the 129 MB L2).
-constexpr size_t kPersistentMaxBytes = 48u << 20;
 constexpr long long kPersistentChunk = 1024;  // steps per persistent launch (bounds a launch's duration)
 constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 
@@ -330,8 +327,7 @@ GridSync grid_sync(lbm13_t h)
 template <typename T, typename C>
 bool use_persistent(lbm13_t h, long long n)
 {
-    if (h->persistent == LBM13_PERSISTENT_OFF || n < 2) return false;
-    if (h->persistent == LBM13_PERSISTENT_AUTO && 2 * h->state_bytes > kPersistentMaxBytes) return false;
+    if (h->persistent != LBM13_PERSISTENT_ON || n < 2) return false;
     if (h->multi_grid < 0) h->multi_grid = multi_grid<T, C>(h->nx, h->ny, h->force);
     if (h->multi_grid <= 0) return false;
     if (!h->sync_mem) {

@@ -78,7 +78,7 @@ __device__ bool grid_barrier(const GridSync &g, unsigned nblocks)
 // One step of the lattice over the whole grid; false if a barrier timed out.
 // The last step of a launch needs no closing barrier (the launch's end is one).
 template <typename T, typename C, bool Force, int R>
-__device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, int ntiles, bool last,
+__device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, int ntiles, bool last, C *slot,
                                           const GridSync &g)
 {
     if (a.any_wall_data) {
@@ -89,7 +89,7 @@ __device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, 
     }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x, ty = t / tiles_x;
-        process_column<T, C, Force, R>(a, tx * 32 + threadIdx.x, (ty * 4 + threadIdx.y) * R);
+        process_column<T, C, Force, R>(a, tx * 32 + threadIdx.x, (ty * 4 + threadIdx.y) * R, slot);
     }
     return last || grid_barrier(g, gridDim.x);
 }
@@ -99,11 +99,13 @@ template <typename T, typename C, bool Force, int R>
 __global__ void __launch_bounds__(128) multi_step_kernel(const StepArgs<T, C> a0, const StepArgs<T, C> a1,
                                                          int nsteps, const GridSync g)
 {
+    __shared__ C slots[128][Q];
+    C *slot = slots[threadIdx.y * 32 + threadIdx.x];
     const int tiles_x = (a0.nx + 31) / 32;
     const int ntiles = tiles_x * ((a0.ny + 4 * R - 1) / (4 * R));
     for (int s = 0; s < nsteps; s += 2) {
-        if (!grid_step<T, C, Force, R>(a0, tiles_x, ntiles, s + 1 >= nsteps, g)) return;
-        if (s + 1 < nsteps && !grid_step<T, C, Force, R>(a1, tiles_x, ntiles, s + 2 >= nsteps, g)) return;
+        if (!grid_step<T, C, Force, R>(a0, tiles_x, ntiles, s + 1 >= nsteps, slot, g)) return;
+        if (s + 1 < nsteps && !grid_step<T, C, Force, R>(a1, tiles_x, ntiles, s + 2 >= nsteps, slot, g)) return;
     }
 }
 

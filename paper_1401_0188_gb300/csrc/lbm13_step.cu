@@ -58,7 +58,10 @@ __global__ void __launch_bounds__(128) batch_wall_kernel(const BatchDesc<T, C> *
 template <typename T, typename C, bool Force, int R>
 __global__ void __launch_bounds__(128) step_kernel(const StepArgs<T, C> a)
 {
-    process_column<T, C, Force, R>(a, blockIdx.x * 32 + threadIdx.x, (blockIdx.y * blockDim.y + threadIdx.y) * R);
+    __shared__ C slots[128][Q];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    process_column<T, C, Force, R>(a, blockIdx.x * 32 + threadIdx.x, (blockIdx.y * blockDim.y + threadIdx.y) * R,
+                                   slots[tid]);
 }
 
 // Many lattices in one launch.  The work list holds (lattice, tile) pairs; a
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(32 * BY, (R == 1 && sizeof(T) == 4) ? 32 / BY 
 {
     __shared__ StepArgs<T, C> sa;
     __shared__ int s_force;
+    __shared__ C slots[32 * BY][Q];
     constexpr int kWords = int(sizeof(StepArgs<T, C>) / 16);
     static_assert(sizeof(StepArgs<T, C>) % 16 == 0, "StepArgs must be a whole number of 16-byte words");
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -104,9 +108,9 @@ __global__ void __launch_bounds__(32 * BY, (R == 1 && sizeof(T) == 4) ? 32 / BY 
             const int y = yb + g * (BY * R);
             if (y >= sa.ny) break;
             if (s_force)
-                process_column<T, C, true, R>(sa, x, y + threadIdx.y * R);
+                process_column<T, C, true, R>(sa, x, y + threadIdx.y * R, slots[tid]);
             else
-                process_column<T, C, false, R>(sa, x, y + threadIdx.y * R);
+                process_column<T, C, false, R>(sa, x, y + threadIdx.y * R, slots[tid]);
         }
         w = wn;
     }

@@ -82,7 +82,7 @@ __device__ __forceinline__ void wall_feq(const Coef<C> &k, const C st[4], C feq[
 // One wall position (or corner) of one lattice: items below 2 ny are the
 // west/east positions, then 2 nx south/north positions, then the 4 corners.
 template <typename T, typename C>
-__device__ __noinline__ void wall_item(const StepArgs<T, C> &a, int item)
+__device__ void wall_item(const StepArgs<T, C> &a, int item)
 {
     const int nx = a.nx, ny = a.ny;
     C st[4], feq[Q];
@@ -115,73 +115,55 @@ __device__ __noinline__ void wall_item(const StepArgs<T, C> &a, int item)
     }
 }
 
-// Source of the population pulled into link j of node (x, y): population js
-// at (xs, ys), as an element offset.  Periodic sides wrap.  A link whose
-// source lies beyond a wall (cross) comes back from the node itself as the
-// opposite population copp(j), from the other of the two wall rows for a
-// distance-2 link normal to the wall; it is negated at a temperature wall's
-// normal links (neg: anti-bounce-back) and gets the wall correction at cp
-// (nullptr when the wall needs no data).  A diagonal beyond two walls at once
-// bounces back with the corner's correction.
-template <typename C>
-struct LinkSrc {
-    long long off;
-    const C *cp;
-    bool cross, neg;
-};
-
+// Value of link j of node (x, y) whose source lies beyond side `side` only.
 template <typename T, typename C>
-__device__ __forceinline__ LinkSrc<C> link_source(const StepArgs<T, C> &a, int j, int x, int y)
+__device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j, int x, int y)
 {
-    int sx = x - cvx(j), sy = y - cvy(j);
-    bool ox = sx < 0 || sx >= a.nx, oy = sy < 0 || sy >= a.ny;
-    if (a.per_x && ox) {
-        sx += sx < 0 ? a.nx : -a.nx;
-        ox = false;
-    }
-    if (a.per_y && oy) {
-        sy += sy < 0 ? a.ny : -a.ny;
-        oy = false;
-    }
-    LinkSrc<C> s;
-    s.cp = nullptr;
-    s.cross = ox || oy;
-    s.neg = false;
-    int js = j, xs = sx, ys = sy;
-    if (ox && oy) {
-        js = copp(j);
-        xs = x;
-        ys = y;
-        const int sxd = sx < 0 ? WEST : EAST, syd = sy < 0 ? SOUTH : NORTH;
-        if (a.wall[sxd].needs_data || a.wall[syd].needs_data)
-            s.cp = a.corr + 16LL * a.corr_stride + ((sxd == EAST ? 1 : 0) + (syd == NORTH ? 2 : 0));
-    } else if (ox || oy) {
-        const int side = ox ? (sx < 0 ? WEST : EAST) : (sy < 0 ? SOUTH : NORTH);
-        const WallArgs<C> &w = a.wall[side];
-        const bool xwall = side <= EAST;
-        js = copp(j);
-        xs = x;
-        ys = y;
-        if (xwall ? cvy(j) == 0 : cvx(j) == 0) {
-            if (xwall && (cvx(j) == 2 || cvx(j) == -2)) xs = side == WEST ? 1 - x : 2 * a.nx - 3 - x;
-            if (!xwall && (cvy(j) == 2 || cvy(j) == -2)) ys = side == SOUTH ? 1 - y : 2 * a.ny - 3 - y;
-            s.neg = w.kind == WALL_MIXED;
-        }
-        if (w.needs_data)
-            s.cp = a.corr + ((long long)side * a.corr_stride + (xwall ? y : x)) * 4 + wall_slot(side, j);
-    }
-    s.off = (long long)js * a.plane + (long long)ys * a.pitch + xs;
-    return s;
+    const int jb = copp(j);
+    const WallArgs<C> &w = a.wall[side];
+    const bool xwall = side <= EAST;
+    const int pos = xwall ? y : x;
+    const C add = w.needs_data ? LBM13_LDG(a.corr + ((long long)side * a.corr_stride + pos) * 4 + wall_slot(side, j))
+                               : C(0);
+    const bool normal = xwall ? cvy(j) == 0 : cvx(j) == 0;
+    if (!normal) return ld(a, jb, x, y) + add;
+    int xf = x, yf = y;
+    if (xwall && (cvx(j) == 2 || cvx(j) == -2)) xf = side == WEST ? 1 - x : 2 * a.nx - 3 - x;
+    if (!xwall && (cvy(j) == 2 || cvy(j) == -2)) yf = side == SOUTH ? 1 - y : 2 * a.ny - 3 - y;
+    const C v = ld(a, jb, xf, yf);
+    return (w.kind == WALL_MIXED ? -v : v) + add;
 }
 
-// The value of link j pulled from its source s.
+// Every link of one node resolved on its own (warps on the bottom/top rows).
 template <typename T, typename C>
-__device__ __forceinline__ C pull(const StepArgs<T, C> &a, const LinkSrc<C> &s)
+__device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int y, C f[Q])
 {
-    const C v = C(LBM13_LDG(a.fin + s.off));
-    if (!s.cross) return v;
-    const C add = s.cp ? C(LBM13_LDG(s.cp)) : C(0);
-    return (s.neg ? -v : v) + add;
+    int sxd = -1, syd = -1;
+    if (!a.per_x) sxd = x <= 1 ? WEST : (x >= a.nx - 2 ? EAST : -1);
+    if (!a.per_y) syd = y <= 1 ? SOUTH : (y >= a.ny - 2 ? NORTH : -1);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        int sx = x - cvx(j), sy = y - cvy(j);
+        bool ox = false, oy = false;
+        if (sx < 0 || sx >= a.nx) {
+            if (a.per_x) sx += sx < 0 ? a.nx : -a.nx;
+            else ox = true;
+        }
+        if (sy < 0 || sy >= a.ny) {
+            if (a.per_y) sy += sy < 0 ? a.ny : -a.ny;
+            else oy = true;
+        }
+        if (!ox && !oy) {
+            f[j] = ld(a, j, sx, sy);
+        } else if (ox && oy) {
+            const int c = (sxd == EAST ? 1 : 0) + (syd == NORTH ? 2 : 0);
+            const C add = (a.wall[sxd].needs_data || a.wall[syd].needs_data) ? LBM13_LDG(a.corr + 16LL * a.corr_stride + c)
+                                                                              : C(0);
+            f[j] = ld(a, copp(j), x, y) + add;
+        } else {
+            f[j] = cross_wall(a, ox ? sxd : syd, j, x, y);
+        }
+    }
 }
 
 template <typename T, typename C>
@@ -194,33 +176,15 @@ __device__ __forceinline__ void store(const StepArgs<T, C> &a, int x, int y, con
 
 // ------------------------------------------------------------- the step
 
-// The 13 pulls of a node whose links may cross an edge, every link through
-// link_source (the loads independent of each other).  Out of line, so that
-// the edge case does not raise the register count of the interior path.
-template <typename T, typename C>
-__device__ __noinline__ void edge_gather(const StepArgs<T, C> &a, int x, int y, C *f)
-{
-#pragma unroll
-    for (int j = 0; j < Q; ++j) f[j] = pull(a, link_source(a, j, x, y));
-}
-
-template <typename T, typename C, bool Force>
-__device__ __forceinline__ void edge_node(const StepArgs<T, C> &a, int x, int y)
-{
-    C f[Q];
-    edge_gather(a, x, y, f);
-    collide<Force>(f, a.k);
-    store(a, x, y, f);
-}
-
 // One thread: R consecutive rows y0..y0+R-1 of column x.  A warp whose rows
 // are all at least two rows away from the bottom and top edges loads its 13
-// pulls with the source column wrapped (periodic x) or clamped into the
-// lattice (uniform code, always in bounds), then collides and stores; at x
-// walls the lanes within two columns of the edge take edge_node instead, and
-// so do all nodes of the warps on the bottom and top rows.
+// pulls with the source column clamped into the lattice (uniform code, always
+// in bounds); lanes within two columns of the left or right edge then replace
+// the links that cross that edge (periodic wrap, or the wall rule with the
+// precomputed correction).  Warps on the bottom or top rows resolve every node
+// with gather_general through `slot`, this thread's shared-memory row.
 template <typename T, typename C, bool Force, int R>
-__device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, int y0)
+__device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, int y0, C *slot)
 {
     const int nx = a.nx, ny = a.ny;
     const bool yin = y0 >= 2 && y0 + R <= ny - 2;
@@ -231,16 +195,25 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int j = 0; j < Q; ++j) {
-                int xs = x - cvx(j);
-                if (a.per_x) xs += xs < 0 ? nx : (xs >= nx ? -nx : 0);
-                xs = min(max(xs, 0), nx - 1);
+                const int xs = min(max(x - cvx(j), 0), nx - 1);
                 f[r][j] = C(LBM13_LDG(base + (long long)j * a.plane + (long long)(r - cvy(j)) * a.pitch + xs));
             }
         }
         if (x >= nx) return;
-        if (!a.per_x && (x < 2 || x >= nx - 2)) {
-            for (int r = 0; r < R; ++r) edge_node<T, C, Force>(a, x, y0 + r);
-            return;
+        if (x < 2 || x >= nx - 2) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    if (cvx(j) == 0) continue;
+                    const int sx = x - cvx(j);
+                    if (sx >= 0 && sx < nx) continue;
+                    if (a.per_x)
+                        f[r][j] = ld(a, j, sx < 0 ? sx + nx : sx - nx, y0 + r - cvy(j));
+                    else
+                        f[r][j] = cross_wall(a, sx < 0 ? WEST : EAST, j, x, y0 + r);
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -251,7 +224,12 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
         for (int r = 0; r < R; ++r) {
             const int y = y0 + r;
             if (y >= ny) break;
-            edge_node<T, C, Force>(a, x, y);
+            C f[Q];
+            gather_general(a, x, y, slot);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) f[j] = slot[j];
+            collide<Force>(f, a.k);
+            store(a, x, y, f);
         }
     }
 }

@@ -11,9 +11,8 @@ memory for the queue.  Admission and retirement happen only between rounds of
 `check_every` steps, so each request sees the same sequence of steps and checks
 whether it runs alone or in a mix: its result does not depend on the mix.
 
-The baseline mode steps each lattice with its own per-step launches in FP64
-(the plain one-lattice-per-launch path, no persistent multi-step launches),
-with the same admission and checks.
+The baseline mode steps each lattice with its own launches in FP64 (the plain
+one-lattice-per-launch path), with the same admission and checks.
 """
 import math
 import time
@@ -140,8 +139,6 @@ class Server:
                     break
                 req = pending.pop(0)
                 lat = lbm13.Lattice(nx, ny, p, bnd, precision=self.precision)
-                if not self.batched:
-                    lat.set_persistent(lbm13.PERSISTENT_OFF)
                 lat.set_state(1.0, 0.0, 0.0, P.rest_temperature(p))
                 lat.residual()
                 active.append(_Active(req, lat, nx, ny, b, now()))

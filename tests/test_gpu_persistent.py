@@ -85,17 +85,17 @@ def test_persistent_runs_longer_than_one_launch(L, pstar):
     assert a.save() == b.save()
 
 
-def test_auto_mode_chooses_by_size(L, pstar):
-    """AUTO: persistent for a lattice whose buffers fit in 48 MB, per-step
-    launches for a larger one (the grid size is reported only when chosen)."""
-    small = L.Lattice(256, 256, pstar, precision=L.FP32_DEVIATION)
-    small.step(4)
-    assert small.info()["persistent_grid"] > 0
-    big = L.Lattice(2048, 2048, pstar, precision=L.FP32_DEVIATION)
-    big.step(4)
-    assert big.info()["persistent_grid"] == 0
+def test_modes(L, pstar):
+    """AUTO (the default) steps launch by launch; ON takes the persistent
+    launch (its grid size is reported once chosen); other modes are refused."""
+    g = L.Lattice(256, 256, pstar, precision=L.FP32_DEVIATION)
+    g.step(4)
+    assert g.info()["persistent_grid"] == 0
+    g.set_persistent(L.PERSISTENT_ON)
+    g.step(4)
+    assert g.info()["persistent_grid"] > 0
     with pytest.raises(L.Lbm13Error):
-        small.set_persistent(7)
+        g.set_persistent(7)
 
 
 def test_barrier_wait_is_bounded(L, pstar):
