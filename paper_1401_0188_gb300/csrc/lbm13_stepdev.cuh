@@ -138,31 +138,49 @@ __device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j
 template <typename T, typename C>
 __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int y, C f[Q])
 {
-    int sxd = -1, syd = -1;
-    if (!a.per_x) sxd = x <= 1 ? WEST : (x >= a.nx - 2 ? EAST : -1);
-    if (!a.per_y) syd = y <= 1 ? SOUTH : (y >= a.ny - 2 ? NORTH : -1);
+    // Branch-free: every link's source offset, sign and correction are chosen
+    // with selects, so the 13 population loads (and the corrections) are
+    // independent and in flight together.
+    const int nx = a.nx, ny = a.ny;
+    const bool px = a.per_x != 0, py = a.per_y != 0;
+    const bool west = x <= 1, south = y <= 1;
+    const int kind_x = west ? a.wall[WEST].kind : a.wall[EAST].kind;
+    const int kind_y = south ? a.wall[SOUTH].kind : a.wall[NORTH].kind;
+    const bool nd_x = (west ? a.wall[WEST].needs_data : a.wall[EAST].needs_data) != 0;
+    const bool nd_y = (south ? a.wall[SOUTH].needs_data : a.wall[NORTH].needs_data) != 0;
+    const long long st = a.corr_stride;
+    const long long row_x = ((long long)(west ? WEST : EAST) * st + y) * 4;
+    const long long row_y = ((long long)(south ? SOUTH : NORTH) * st + x) * 4;
+    const long long corner = 16LL * st + (west ? 0 : 1) + (south ? 0 : 2);
+    C v[Q], ad[Q];
+    unsigned cross = 0u, neg = 0u;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         int sx = x - cvx(j), sy = y - cvy(j);
-        bool ox = false, oy = false;
-        if (sx < 0 || sx >= a.nx) {
-            if (a.per_x) sx += sx < 0 ? a.nx : -a.nx;
-            else ox = true;
-        }
-        if (sy < 0 || sy >= a.ny) {
-            if (a.per_y) sy += sy < 0 ? a.ny : -a.ny;
-            else oy = true;
-        }
-        if (!ox && !oy) {
-            f[j] = ld(a, j, sx, sy);
-        } else if (ox && oy) {
-            const int c = (sxd == EAST ? 1 : 0) + (syd == NORTH ? 2 : 0);
-            const C add = (a.wall[sxd].needs_data || a.wall[syd].needs_data) ? LBM13_LDG(a.corr + 16LL * a.corr_stride + c)
-                                                                              : C(0);
-            f[j] = ld(a, copp(j), x, y) + add;
-        } else {
-            f[j] = cross_wall(a, ox ? sxd : syd, j, x, y);
-        }
+        const bool bx = sx < 0 || sx >= nx, by = sy < 0 || sy >= ny;
+        const bool ox = bx && !px, oy = by && !py;
+        sx += sx < 0 ? nx : (sx >= nx ? -nx : 0);
+        sy += sy < 0 ? ny : (sy >= ny ? -ny : 0);
+        const bool c = ox || oy, both = ox && oy;
+        int xs = c ? x : sx, ys = c ? y : sy;
+        if (cvy(j) == 0 && (cvx(j) == 2 || cvx(j) == -2) && ox) xs = west ? 1 - x : 2 * nx - 3 - x;
+        if (cvx(j) == 0 && (cvy(j) == 2 || cvy(j) == -2) && oy) ys = south ? 1 - y : 2 * ny - 3 - y;
+        const int js = c ? copp(j) : j;
+        const bool n = (ox && !oy && cvy(j) == 0 && kind_x == WALL_MIXED) ||
+                       (oy && !ox && cvx(j) == 0 && kind_y == WALL_MIXED);
+        const bool has = both ? (nd_x || nd_y) : (ox ? nd_x : (oy ? nd_y : false));
+        const int slot_x = west ? wall_slot(WEST, j) : wall_slot(EAST, j);
+        const int slot_y = south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j);
+        const long long coff = both ? corner : (ox ? row_x + slot_x : row_y + slot_y);
+        v[j] = C(LBM13_LDG(a.fin + (long long)js * a.plane + (long long)ys * a.pitch + xs));
+        ad[j] = has ? C(LBM13_LDG(a.corr + coff)) : C(0);
+        cross |= (c ? 1u : 0u) << j;
+        neg |= (n ? 1u : 0u) << j;
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const C w = ((neg >> j) & 1u) ? -v[j] : v[j];
+        f[j] = ((cross >> j) & 1u) ? w + ad[j] : v[j];
     }
 }
 
