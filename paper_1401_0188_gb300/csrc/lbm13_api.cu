@@ -467,6 +467,17 @@ int lbm13_derive(const lbm13_params *params, double *out)
     return derive(*params, out);
 }
 
+int lbm13_linear_growth(const lbm13_params *params, double ux, double uy, int n, double *growth)
+{
+    if (!params || !growth || n < 1 || n > 129) return fail(nullptr, LBM13_EINVAL, "NULL argument or n outside 1..129");
+    double D[LBM13_DERIVED_COUNT];
+    const int st = derive(*params, D);
+    if (st != LBM13_OK) return fail(nullptr, st, "parameter set rejected by lbm13_derive");
+    if (linear_growth(*params, D, ux, uy, n, growth) != LBM13_OK)
+        return fail(nullptr, LBM13_EINVAL, "eigenvalue iteration did not converge");
+    return LBM13_OK;
+}
+
 const char *lbm13_last_error(lbm13_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary, int precision,

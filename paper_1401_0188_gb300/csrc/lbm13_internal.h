@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm13_math.cuh"
+#include "../../include/lbm13.h"
 
 namespace lbm13 {
 
@@ -96,6 +97,12 @@ cudaError_t launch_multi(const StepArgs<T, C> &a0, const StepArgs<T, C> &a1, boo
 // `rounds` grid barriers over `grid` blocks that wait for expect_blocks
 // arrivals (expect_blocks > grid makes every wait run out).
 cudaError_t launch_barrier_check(int grid, unsigned expect_blocks, int rounds, const GridSync &g, cudaStream_t s);
+
+// Linear stability (lbm13_linear.cu, host): the largest |z| - 1 over the
+// eigenvalues z of the linearised step about (rho, j, E) = (1, (ux, uy),
+// E0 + 13 |u|^2) for the n x n wave vectors of [-pi, pi]^2.  D = the derived
+// constants of lbm13_derive.  LBM13_EINVAL if an eigenvalue iteration fails.
+int linear_growth(const lbm13_params &p, const double *D, double ux, double uy, int n, double *growth);
 
 // Rest moments used by the read-outs (double precision).
 struct Rest {

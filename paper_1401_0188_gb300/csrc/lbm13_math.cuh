@@ -168,6 +168,21 @@ LBM13_HD double recip(double x)
 }
 LBM13_HD float recip(float x) { return 1.0f / x; }
 
+// 1/rho for the collision, where it only scales second-order terms (the
+// momentum-flux equilibria j_x^2 - j_y^2 and j_x j_y, the force's work): one
+// Newton step after the FP32 seed leaves a relative error near 2^-47, i.e.
+// below 1e-18 in those terms at |u| ~ 0.01.
+LBM13_HD double recip_uu(double x)
+{
+#ifdef __CUDA_ARCH__
+    const double r = double(1.0f / float(x));
+    return fma(r, fma(-x, r, 1.0), r);
+#else
+    return 1.0 / x;
+#endif
+}
+LBM13_HD float recip_uu(float x) { return 1.0f / x; }
+
 // One collision in place (deviation form).  Equilibria of Sec. 2, Eq.
 // (d2q13-moments-equil) at j + F/2 and E + 13 q; the nine non-conserved
 // moments relax as m* = m + s (m_eq - m); j* = j + F and
@@ -198,7 +213,7 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
     const C rx = C(4) * b1 + C(-3) * dm + b9;
     const C ry = C(4) * b2 + C(-3) * dp + b10;
     const C rho = C(1) + drho;
-    const C inv_rho = recip(rho);
+    const C inv_rho = recip_uu(rho);
     C Fx = C(0), Fy = C(0), jxh = jx, jyh = jy;
     if (Force) {
         const C w = rho - k.rho_ref;
@@ -230,8 +245,9 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
     const C drx = k.l_r * (jxh * R1 - rx), dry = k.l_r * (jyh * R1 - ry);
     // tensor block: XX, XY toward the momentum flux, XXe toward 0
     const C XXeq = (jxh * jxh - jyh * jyh) * inv_rho;
-    const C t1 = k.l_XX * XXeq + k.t1X1 * X1 + k.t1X9 * X9;
-    const C t9 = C(4) * k.l_XX * XXeq + k.t9X1 * X1 + k.t9X9 * X9;
+    const C XXl = k.l_XX * XXeq;
+    const C t1 = XXl + k.t1X1 * X1 + k.t1X9 * X9;
+    const C t9 = C(4) * XXl + k.t9X1 * X1 + k.t9X9 * X9;
     const C dXY = k.l_XY * (jxh * jyh * inv_rho - X5);
     // back to populations through the pairs
     const C o1 = djx + C(-2) * dqx + C(4) * drx;
