@@ -180,10 +180,22 @@ const char *lbm13_status_string(int status);
  * LBM13_EUNSTABLE when sigma_q <= 0 (out is filled in both cases). */
 int lbm13_derive(const lbm13_params *params, double *out);
 
+/* Host-only: linear stability of the time step about the uniform state
+ * rho = 1, u = (ux, uy), T = T0 (no force), the procedure of the end of Sec. 2:
+ * *growth = max |z| - 1 over the eigenvalues z of the linearised step for the
+ * n x n wave vectors k = (-pi + 2 pi a/(n-1), -pi + 2 pi b/(n-1)) (k = 0 for
+ * n = 1).  The step is linearly stable when *growth <= ~1e-12 (round-off).
+ * n in 1..129.  LBM13_EINVAL for NULL, n out of range or an eigenvalue
+ * iteration that does not converge; lbm13_derive's status when it rejects the
+ * parameter set. */
+int lbm13_linear_growth(const lbm13_params *params, double ux, double uy, int n, double *growth);
+
 /* Create an nx x ny lattice (nx, ny >= 2; >= 4 along an axis that has walls;
  * nx <= 2^20, ny <= 32768, nx * ny < 2^31) on the current CUDA device.  `alloc` may be NULL (cudaMalloc),
  * `stream` is a cudaStream_t (NULL = legacy default stream).  The state starts
- * at rest: rho = 1, u = 0, T = T0.  On success *out is a new handle. */
+ * at rest: rho = 1, u = 0, T = T0.  On success *out is a new handle.
+ * LBM13_EUNSTABLE when sigma_q <= 0 or when the linearised step at rest
+ * amplifies a Fourier mode (lbm13_linear_growth on a 9 x 9 k-grid above 1e-9). */
 int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary,
                  int precision, const lbm13_allocator *alloc, void *stream, lbm13_t *out);
 

@@ -140,6 +140,12 @@ bool finite_all(std::initializer_list<double> v)
 // relaxation time sigma_XX = 104 nu / A of the basis.  Fills out[] and returns a
 // status: EINVAL for a rate outside (0, 2) or a non-positive viscosity, Prandtl
 // number or A; EUNSTABLE when sigma_q <= 0.
+// The rest-state scan of lbm13_create: wave vectors on a 9 x 9 grid of
+// [-pi, pi]^2 (the edges, the origin and the diagonals included), and the
+// round-off margin on |z| - 1.
+constexpr int kCreateScanN = 9;
+constexpr double kCreateScanTol = 1e-9;
+
 int derive(const lbm13_params &p, double *out)
 {
     for (int i = 0; i < LBM13_DERIVED_COUNT; ++i) out[i] = 0.0;
@@ -515,6 +521,15 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
         delete h;
         return fail(nullptr, st, st == LBM13_EUNSTABLE ? "sigma_q <= 0: no positive relaxation time for q"
                                                        : "parameter out of range (rates in (0,2), nu > 0, Pr > 0)");
+    }
+    // the linearised step at rest must not amplify any Fourier mode
+    double growth = 0.0;
+    if (linear_growth(h->p, h->derived, 0.0, 0.0, kCreateScanN, &growth) != LBM13_OK || !(growth <= kCreateScanTol)) {
+        delete h;
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "linearly unstable at rest: max |z| - 1 = %.3g over a %d x %d k-grid",
+                      growth, kCreateScanN, kCreateScanN);
+        return fail(nullptr, LBM13_EUNSTABLE, msg);
     }
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();

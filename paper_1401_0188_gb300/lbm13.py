@@ -37,7 +37,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
-           "lbm13_set_persistent", "lbm13_barrier_check")
+           "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth")
 
 
 class Lbm13Error(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
         "lbm13_residual": (C.c_int, [vp, dp]),
         "lbm13_project": (C.c_int, [vp, C.c_int, C.c_int, dp]),
         "lbm13_set_persistent": (C.c_int, [vp, C.c_int]),
+        "lbm13_linear_growth": (C.c_int, [C.POINTER(Params), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]),
         "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
@@ -159,6 +160,15 @@ def make_boundary(b):
     return Boundary(mk(b["west"]), mk(b["east"]), mk(b["south"]), mk(b["north"]),
                     float(b.get("gx", 0.0)), float(b.get("gy", 0.0)), float(b.get("rho_ref", 0.0)),
                     int(b.get("wall_density", 0)), float(b.get("heat", 0.0)))
+
+
+def linear_growth(params, ux=0.0, uy=0.0, n=9):
+    """max |z| - 1 of the linearised step about rho = 1, u = (ux, uy), T = T0
+    over an n x n grid of wave vectors in [-pi, pi]^2 (host only, no GPU)."""
+    out = C.c_double(0.0)
+    pp = make_params(params)
+    _check(lib().lbm13_linear_growth(C.byref(pp), float(ux), float(uy), int(n), C.byref(out)))
+    return out.value
 
 
 def barrier_check(blocks, extra_blocks, timeout_s):

@@ -58,3 +58,32 @@ def test_select_refuses_unknown_region():
         params.select(0.006, 0.99)
     assert params.stable_viscosity(0.004, 0.95) == 0.005
     assert params.stable_viscosity(0.004, 0.99) == 0.01
+
+
+@pytest.mark.parametrize("nu,Pr,U", [(0.05, 0.71, (0.0, 0.0)), (0.05, 0.71, (0.03, 0.0)), (0.02, 0.5, (0.02, 0.01)),
+                                     (0.005, 0.71, (0.0, 0.0)), (0.05, 1.0, (0.0212, 0.0212))])
+def test_library_scan_matches_numpy_scan(nu, Pr, U):
+    """The C++ eigenvalue scan (Hessenberg + shifted QR) behind lbm13_create
+    agrees with the numpy scan of the same linearised step, stable and unstable
+    sets alike."""
+    from paper_1401_0188_gb300 import lbm13
+    p = params.pstar(nu, Pr)
+    g_lib = lbm13.linear_growth(p, U[0], U[1], 13)
+    g_np = stability.max_growth(p, (U,), 13)
+    assert g_lib == pytest.approx(g_np, abs=1e-10)
+
+
+def test_create_rejects_a_linearly_unstable_set():
+    """lbm13_create refuses pstar at nu = 0.005 (unstable at rest) with
+    LBM13_EUNSTABLE before touching a device, and accepts the set select()
+    gives for the same viscosity as far as the scan goes."""
+    import ctypes
+    from paper_1401_0188_gb300 import lbm13
+    L = lbm13.lib()
+    bnd = lbm13.make_boundary(lbm13.boundary())
+    h = ctypes.c_void_p()
+    st = L.lbm13_create(16, 16, ctypes.byref(lbm13.make_params(params.pstar(0.005, 0.71))), ctypes.byref(bnd), 0,
+                        None, None, ctypes.byref(h))
+    assert st == 3 and not h.value
+    assert b"linearly unstable" in L.lbm13_last_error(None)
+    assert lbm13.linear_growth(params.select(0.005, 0.71)) < 1e-12
