@@ -28,17 +28,16 @@ __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
 
 // ------------------------------------------------------ boundary links
 
-// Wall state at position `pos` along side S: st = (drho_w, dE_w, ux_w, uy_w).
-// The side is a template argument so that every population index is a
-// compile-time constant (the arrays stay in registers).
-template <int S, typename T, typename C>
-__device__ __forceinline__ void wall_state(const StepArgs<T, C> &a, int pos, C st[4])
+// Wall state at position `pos` along side `s`: st = (drho_w, dE_w, ux_w, uy_w).
+template <typename T, typename C>
+__device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[4])
 {
-    const WallArgs<C> &w = a.wall[S];
-    const int x0 = S == WEST ? 0 : S == EAST ? a.nx - 1 : pos;
-    const int x1 = S == WEST ? 1 : S == EAST ? a.nx - 2 : pos;
-    const int y0 = S == SOUTH ? 0 : S == NORTH ? a.ny - 1 : pos;
-    const int y1 = S == SOUTH ? 1 : S == NORTH ? a.ny - 2 : pos;
+    const WallArgs<C> &w = a.wall[s];
+    int x0, y0, x1, y1;
+    if (s == WEST) { x0 = 0; x1 = 1; y0 = y1 = pos; }
+    else if (s == EAST) { x0 = a.nx - 1; x1 = a.nx - 2; y0 = y1 = pos; }
+    else if (s == SOUTH) { y0 = 0; y1 = 1; x0 = x1 = pos; }
+    else { y0 = a.ny - 1; y1 = a.ny - 2; x0 = x1 = pos; }
     C g0[Q], g1[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -51,8 +50,8 @@ __device__ __forceinline__ void wall_state(const StepArgs<T, C> &a, int pos, C s
         // so the anti-bounce-back links return 2 rho_w e_j; rho_w balances the
         // outgoing normal populations (unit link from the first node, the
         // distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two)
-        constexpr int ja = S == WEST ? 3 : S == EAST ? 1 : S == SOUTH ? 4 : 2;
-        constexpr int jb = S == WEST ? 11 : S == EAST ? 9 : S == SOUTH ? 12 : 10;
+        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
+        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
         C e[Q];
         equilibrium_dev(C(0), w.eT + C(13) * (w.ux * w.ux + w.uy * w.uy), w.ux, w.uy, a.k, e);
         const C ea = C(0.5) * (e[ja] + e[copp(ja)]), eb = C(0.5) * (e[jb] + e[copp(jb)]);
@@ -80,57 +79,39 @@ __device__ __forceinline__ void wall_feq(const Coef<C> &k, const C st[4], C feq[
     equilibrium_dev(st[0], st[1], rho * st[2], rho * st[3], k, feq);
 }
 
-// The four corrections of wall position `pos` on side S.
-template <int S, typename T, typename C>
-__device__ __forceinline__ void wall_side_item(const StepArgs<T, C> &a, int pos)
-{
-    const WallArgs<C> &w = a.wall[S];
-    if (w.kind == PERIODIC || !w.needs_data) return;
-    C st[4], feq[Q];
-    wall_state<S>(a, pos, st);
-    wall_feq(a.k, st, feq);
-    C *out = a.corr + ((long long)S * a.corr_stride + pos) * 4;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int j = wall_link(S, i), jb = copp(j);
-        const bool normal = S <= EAST ? cvy(j) == 0 : cvx(j) == 0;
-        out[i] = (w.kind == WALL_MIXED && normal) ? feq[j] + feq[jb] : feq[j] - feq[jb];
-    }
-}
-
-// The correction of corner CR (0: x=0,y=0; 1: x=nx-1,y=0; 2: x=0,y=ny-1;
-// 3: x=nx-1,y=ny-1): bounce-back with the mean of the two walls' states.
-template <int CR, typename T, typename C>
-__device__ __forceinline__ void wall_corner_item(const StepArgs<T, C> &a)
-{
-    constexpr int SX = (CR & 1) ? EAST : WEST, SY = (CR & 2) ? NORTH : SOUTH;
-    if (a.per_x || a.per_y || !(a.wall[SX].needs_data || a.wall[SY].needs_data)) return;
-    C s1[4], s2[4], st[4], feq[Q];
-    wall_state<SX>(a, (CR & 2) ? a.ny - 1 : 0, s1);
-    wall_state<SY>(a, (CR & 1) ? a.nx - 1 : 0, s2);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) st[i] = C(0.5) * (s1[i] + s2[i]);
-    wall_feq(a.k, st, feq);
-    constexpr int j = corner_link(CR);
-    a.corr[16LL * a.corr_stride + CR] = feq[j] - feq[copp(j)];
-}
-
 // One wall position (or corner) of one lattice: items below 2 ny are the
 // west/east positions, then 2 nx south/north positions, then the 4 corners.
 template <typename T, typename C>
-__device__ __noinline__ void wall_item(const StepArgs<T, C> &a, int item)
+__device__ void wall_item(const StepArgs<T, C> &a, int item)
 {
     const int nx = a.nx, ny = a.ny;
-    if (item < ny) wall_side_item<WEST>(a, item);
-    else if (item < 2 * ny) wall_side_item<EAST>(a, item - ny);
-    else if (item < 2 * ny + nx) wall_side_item<SOUTH>(a, item - 2 * ny);
-    else if (item < 2 * ny + 2 * nx) wall_side_item<NORTH>(a, item - 2 * ny - nx);
-    else {
+    C st[4], feq[Q];
+    if (item < 2 * ny + 2 * nx) {
+        const int s = item < 2 * ny ? (item < ny ? WEST : EAST) : (item - 2 * ny < nx ? SOUTH : NORTH);
+        const int pos = item < 2 * ny ? item % ny : (item - 2 * ny) % nx;
+        const WallArgs<C> &w = a.wall[s];
+        if (w.kind == PERIODIC || !w.needs_data) return;
+        wall_state(a, s, pos, st);
+        wall_feq(a.k, st, feq);
+        C *out = a.corr + ((long long)s * a.corr_stride + pos) * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = wall_link(s, i), jb = copp(j);
+            const bool normal = s <= EAST ? cvy(j) == 0 : cvx(j) == 0;
+            out[i] = (w.kind == WALL_MIXED && normal) ? feq[j] + feq[jb] : feq[j] - feq[jb];
+        }
+    } else if (item < 2 * ny + 2 * nx + 4) {
         const int c = item - 2 * ny - 2 * nx;
-        if (c == 0) wall_corner_item<0>(a);
-        else if (c == 1) wall_corner_item<1>(a);
-        else if (c == 2) wall_corner_item<2>(a);
-        else if (c == 3) wall_corner_item<3>(a);
+        const int sx = (c & 1) ? EAST : WEST, sy = (c & 2) ? NORTH : SOUTH;
+        if (a.per_x || a.per_y || !(a.wall[sx].needs_data || a.wall[sy].needs_data)) return;
+        C s1[4], s2[4];
+        wall_state(a, sx, (c & 2) ? ny - 1 : 0, s1);
+        wall_state(a, sy, (c & 1) ? nx - 1 : 0, s2);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[i] = C(0.5) * (s1[i] + s2[i]);
+        wall_feq(a.k, st, feq);
+        const int j = corner_link(c);
+        a.corr[16LL * a.corr_stride + c] = feq[j] - feq[copp(j)];
     }
 }
 
