@@ -133,3 +133,50 @@ def test_plan_rejects_bad_lattice_lists(L):
     with pytest.raises(L.Lbm13Error):
         plan.step(-1)
     plan.close()
+
+
+def test_full_batched_workload(L):
+    """The bench's batched workload at full size: 256 cavities (19.7 M nodes,
+    sides 64..512, Ra 1e3..1e6, Pr 0.5..1.0, FP32-deviation) in the
+    configuration the autotuner picks on GB300 (one row per thread, 4 warps, one
+    block per tile, largest lattice first, 4 row groups).  After 6 steps from
+    rest every lattice is bit-identical to the same lattice stepped alone, and
+    the first 64 x 64 cavity agrees with the FP64 oracle within the FP32 bounds."""
+    import os
+    import torch
+    from oracle import oracle as O
+    from paper_1401_0188_gb300 import serving as S
+    reqs = S.batch_workload(256)
+    setups = [S.request_setup(r) for r in reqs]
+
+    def make():
+        out = []
+        for nx, ny, p, bnd in setups:
+            g = L.Lattice(nx, ny, p, bnd, precision=L.FP32_DEVIATION)
+            g.set_state(1.0, 0.0, 0.0, (p["E0"] + 28) / 26)
+            out.append(g)
+        return out
+
+    a = make()
+    plan = L.Plan(a)
+    plan.set_config(1, 4, 0, 2, 4)
+    plan.step(6)
+    plan_state = [g.save() for g in a]
+    plan.close()
+    for g in a:
+        g.close()
+    del a
+    torch.cuda.empty_cache()
+    b = make()
+    for g in b:
+        g.step(6)
+    assert all(g.save() == s for g, s in zip(b, plan_state))
+    i = next(k for k, (nx, ny, _, _) in enumerate(setups) if nx == 64)
+    nx, ny, p, bnd = setups[i]
+    o = O.Lattice(nx, ny, p, bnd, nthreads=max(1, os.cpu_count() or 1))
+    o.set_equilibrium(1.0, 0.0, 0.0, (p["E0"] + 28) / 26)
+    o.step(6)
+    mo, mg = o.macro(), b[i].macro()
+    assert np.abs(mo - mg).max() <= 1e-7
+    for g in b:
+        g.close()
