@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm13.h"
 #include "lbm13_internal.h"
 
@@ -89,6 +91,15 @@ int cuda_fail(lbm13_t h, cudaError_t e, const char *where)
         const int rc_ = check_barrier_error(h);           \
         if (rc_ != LBM13_OK) return rc_;                  \
     } while (0)
+
+// NVTX range over one entry point (a no-op unless a profiler is attached), so
+// that a timeline shows steps, read-outs and plan calls by name.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Keeps the lattice's device current for the duration of a call.
 struct DeviceGuard {
@@ -667,6 +678,7 @@ int lbm13_set_state_device(lbm13_t h, const double *rho, const double *ux, const
 
 int lbm13_set_state(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T)
 {
+    Range range_("lbm13_set_state");
     if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
     DeviceGuard g(h->device);
     const size_t n = size_t(h->nx) * h->ny, bytes = n * sizeof(double);
@@ -779,6 +791,7 @@ int lbm13_restore(lbm13_t h, const void *host, size_t bytes)
 
 int lbm13_step(lbm13_t h, int64_t n)
 {
+    Range range_("lbm13_step");
     if (!h || n < 0) return fail(h, LBM13_EINVAL, "NULL handle or negative step count");
     if (n == 0) return LBM13_OK;
     DeviceGuard g(h->device);
@@ -799,6 +812,7 @@ int lbm13_moments_device(lbm13_t h, double *out, unsigned mask)
 
 int lbm13_moments(lbm13_t h, double *out, unsigned mask)
 {
+    Range range_("lbm13_moments");
     if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
     if (mask == 0 || (mask >> 18) != 0) return fail(h, LBM13_EINVAL, "mask must select bits 0..17");
     DeviceGuard g(h->device);
@@ -820,6 +834,7 @@ int lbm13_moments(lbm13_t h, double *out, unsigned mask)
 
 int lbm13_residual(lbm13_t h, double *out)
 {
+    Range range_("lbm13_residual");
     if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
     DeviceGuard g(h->device);
     int rc = ensure_reduce(h);
@@ -836,6 +851,7 @@ int lbm13_residual(lbm13_t h, double *out)
 
 int lbm13_project(lbm13_t h, int kx, int ky, double *out)
 {
+    Range range_("lbm13_project");
     if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
     DeviceGuard g(h->device);
     if (!h->proj_mem) {
@@ -904,7 +920,7 @@ struct lbm13_plan {
     size_t work_bytes = 0;
     int ntiles = 0;
     double *res_dev = nullptr;  // [count][16] results of lbm13_plan_residual
-    void *wlats = nullptr;  // indices of the lattices whose walls need data
+    void *wlats = nullptr;  // (lattice, first wall item) per block of the boundary-link launch
     size_t wlats_bytes = 0;
     int nwlats = 0;
     long long nodes = 0;
@@ -967,12 +983,18 @@ int plan_upload_descs(lbm13_plan_t p)
         host[i].tiles_x = (h->nx + 31) / 32;
         p->cur0[i] = h->cur;
     }
-    std::vector<int> wl;
-    for (size_t i = 0; i < p->lats.size(); ++i)
-        if (p->lats[i]->any_wall_data) wl.push_back(int(i));
+    // boundary-link work: one block of kWallBlock items per entry, so that the
+    // wall positions of a large lattice are spread over many blocks
+    std::vector<int2> wl;
+    for (size_t i = 0; i < p->lats.size(); ++i) {
+        lbm13_t h = p->lats[i];
+        if (!h->any_wall_data) continue;
+        const int items = 2 * (h->nx + h->ny) + 4;
+        for (int b = 0; b < items; b += kWallBlock) wl.push_back(make_int2(int(i), b));
+    }
     p->nwlats = int(wl.size());
     if (!wl.empty()) {
-        const size_t wb = wl.size() * sizeof(int);
+        const size_t wb = wl.size() * sizeof(int2);
         if (!p->wlats || p->wlats_bytes < wb) {
             plan_free(p, p->wlats);
             p->wlats = plan_alloc(p, wb);
@@ -1049,13 +1071,13 @@ cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
     cudaError_t e;
     if (p->precision == LBM13_FP64) {
         const auto *d = static_cast<const BatchDesc<double, double> *>(p->desc);
-        e = launch_batch_walls<double, double>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
+        e = launch_batch_walls<double, double>(d, static_cast<const int2 *>(p->wlats), p->nwlats, parity, s);
         if (e != cudaSuccess) return e;
         return launch_batch<double, double>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
                                             p->groups, p->grid, s);
     }
     const auto *d = static_cast<const BatchDesc<float, float> *>(p->desc);
-    e = launch_batch_walls<float, float>(d, static_cast<const int *>(p->wlats), p->nwlats, parity, s);
+    e = launch_batch_walls<float, float>(d, static_cast<const int2 *>(p->wlats), p->nwlats, parity, s);
     if (e != cudaSuccess) return e;
     return launch_batch<float, float>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
                                       p->groups, p->grid, s);
@@ -1205,6 +1227,7 @@ int lbm13_plan_config(lbm13_plan_t p, int64_t out[9])
 
 int lbm13_plan_step(lbm13_plan_t p, int64_t n)
 {
+    Range range_("lbm13_plan_step");
     if (!p || n < 0) return pfail(p, LBM13_EINVAL, "NULL plan or negative step count");
     DeviceGuard g(p->device);
     return plan_steps(p, n);
@@ -1212,6 +1235,7 @@ int lbm13_plan_step(lbm13_plan_t p, int64_t n)
 
 int lbm13_plan_residual(lbm13_plan_t p, double *out)
 {
+    Range range_("lbm13_plan_residual");
     if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");
     DeviceGuard g(p->device);
     const size_t bytes = p->lats.size() * 16 * sizeof(double);
@@ -1240,6 +1264,7 @@ int lbm13_plan_residual(lbm13_plan_t p, double *out)
 
 int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step)
 {
+    Range range_("lbm13_plan_tune");
     if (!p || steps_per_candidate < 1) return pfail(p, LBM13_EINVAL, "NULL plan or steps_per_candidate < 1");
     DeviceGuard g(p->device);
     static const int shapes[][2] = {{1, 4}, {2, 4}, {4, 4}, {2, 2}, {1, 8}};

@@ -131,9 +131,11 @@ inline long long corr_count(int nx, int ny) { return 16LL * (nx > ny ? nx : ny) 
 template <typename T, typename C>
 cudaError_t launch_walls(const StepArgs<T, C> &a, cudaStream_t s);
 
-// Boundary-link kernel of a batch: one block per listed lattice.
+// Boundary-link kernel of a batch: one block of kWallBlock threads per work
+// entry (lattice, first wall item), each thread one wall item.
+constexpr int kWallBlock = 128;
 template <typename T, typename C>
-cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int *lats, int nlats, int parity, cudaStream_t s);
+cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int2 *work, int nwork, int parity, cudaStream_t s);
 
 // Tile shapes (rows per thread R, warps per block BY) of the batched kernel.
 bool batch_shape_supported(int R, int BY);

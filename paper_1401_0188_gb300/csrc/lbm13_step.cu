@@ -46,12 +46,13 @@ __global__ void __launch_bounds__(128) wall_kernel(const StepArgs<T, C> a)
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(128) batch_wall_kernel(const BatchDesc<T, C> *__restrict__ descs,
-                                                        const int *__restrict__ lats, int parity)
+__global__ void __launch_bounds__(kWallBlock) batch_wall_kernel(const BatchDesc<T, C> *__restrict__ descs,
+                                                               const int2 *__restrict__ work, int parity)
 {
-    const StepArgs<T, C> &a = descs[lats[blockIdx.x]].a[parity];
-    const int items = 2 * (a.nx + a.ny) + 4;
-    for (int i = threadIdx.x; i < items; i += blockDim.x) wall_item(a, i);
+    const int2 w = work[blockIdx.x];
+    const StepArgs<T, C> &a = descs[w.x].a[parity];
+    const int item = w.y + int(threadIdx.x);
+    if (item < 2 * (a.nx + a.ny) + 4) wall_item(a, item);
 }
 
 // One lattice: block 32 x 4 threads, each thread R rows of one column.
@@ -136,10 +137,10 @@ cudaError_t launch_walls(const StepArgs<T, C> &a, cudaStream_t s)
 }
 
 template <typename T, typename C>
-cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int *lats, int nlats, int parity, cudaStream_t s)
+cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int2 *work, int nwork, int parity, cudaStream_t s)
 {
-    if (nlats <= 0) return cudaSuccess;
-    batch_wall_kernel<T, C><<<nlats, 128, 0, s>>>(descs, lats, parity);
+    if (nwork <= 0) return cudaSuccess;
+    batch_wall_kernel<T, C><<<nwork, kWallBlock, 0, s>>>(descs, work, parity);
     return cudaGetLastError();
 }
 
@@ -181,9 +182,9 @@ cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int nti
 
 template cudaError_t launch_walls<double, double>(const StepArgs<double, double> &, cudaStream_t);
 template cudaError_t launch_walls<float, float>(const StepArgs<float, float> &, cudaStream_t);
-template cudaError_t launch_batch_walls<double, double>(const BatchDesc<double, double> *, const int *, int, int,
+template cudaError_t launch_batch_walls<double, double>(const BatchDesc<double, double> *, const int2 *, int, int,
                                                         cudaStream_t);
-template cudaError_t launch_batch_walls<float, float>(const BatchDesc<float, float> *, const int *, int, int,
+template cudaError_t launch_batch_walls<float, float>(const BatchDesc<float, float> *, const int2 *, int, int,
                                                       cudaStream_t);
 template cudaError_t launch_step<double, double>(const StepArgs<double, double> &, bool, cudaStream_t);
 template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, bool, cudaStream_t);

@@ -109,8 +109,12 @@ class _Active:
 
 
 class Server:
+    """`backend` provides Lattice and Plan (the CUDA binding by default; the
+    CPU tests of the admission logic pass a stand-in)."""
+
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
-                 max_steps=2_000_000, batched=True, realtime=True):
+                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13):
+        self.backend = backend
         self.precision = precision
         self.hbm_budget = hbm_budget
         self.max_slots = max_slots
@@ -138,7 +142,7 @@ class Server:
                         raise ValueError(f"request {pending[0].rid} needs {b} bytes, above the budget")
                     break
                 req = pending.pop(0)
-                lat = lbm13.Lattice(nx, ny, p, bnd, precision=self.precision)
+                lat = self.backend.Lattice(nx, ny, p, bnd, precision=self.precision)
                 lat.set_state(1.0, 0.0, 0.0, P.rest_temperature(p))
                 lat.residual()
                 active.append(_Active(req, lat, nx, ny, b, now()))
@@ -156,7 +160,7 @@ class Server:
                 if changed or plan is None:
                     if plan is not None:
                         plan.close()
-                    plan = lbm13.Plan([a.lat for a in active])
+                    plan = self.backend.Plan([a.lat for a in active])
                     plan.set_config(1, 4, 0, 2, 1)
                 plan.step(self.check_every)
                 res = plan.residual(raise_on_divergence=False)

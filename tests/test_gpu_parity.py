@@ -330,3 +330,54 @@ def test_full_size_sampled_nodes_match_oracle(L, pstar, n, prec, steps):
         o.step(steps)
         mo = o.macro()[:, r, r]
         assert np.abs(mo - full[:, y, x]).max() <= tol, ((x, y), mo, full[:, y, x])
+
+
+def test_allocator_failure_is_reported(L, pstar):
+    """Injected on the host: a caller allocator that returns NULL.  Creation
+    fails with LBM13_ENOMEM when a population or wall buffer cannot be had; a
+    lattice whose first read-out cannot get its reduction buffers reports
+    LBM13_ENOMEM, keeps its state, and works once memory is available again."""
+    import ctypes
+    import torch
+    lib = L.lib()
+    T0 = _T0(pstar)
+    live = {}
+    budget = {"n": 0}
+
+    def _alloc(size, ctx):
+        if budget["n"] <= 0:
+            return None
+        budget["n"] -= 1
+        ptr = torch.cuda.caching_allocator_alloc(int(size), device=0, stream=torch.cuda.current_stream(0))
+        live[ptr] = size
+        return ptr
+
+    def _free(ptr, ctx):
+        if ptr in live:
+            del live[ptr]
+            torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = L.ALLOC_FN(_alloc), L.FREE_FN(_free)
+    alloc = L.Allocator(fa, ff, None)
+    params = L.make_params(pstar)
+    bnd = L.make_boundary(W.cavity(T0, 0.01, 2e-4))
+    stream = ctypes.c_void_p(torch.cuda.current_stream(0).cuda_stream)
+    for n in (0, 1, 2):   # buffer 0, buffer 1, wall corrections
+        budget["n"] = n
+        h = ctypes.c_void_p()
+        st = lib.lbm13_create(48, 40, ctypes.byref(params), ctypes.byref(bnd), 0, ctypes.byref(alloc), stream,
+                              ctypes.byref(h))
+        assert st == 2 and not h.value, (n, st)
+        assert not live
+    budget["n"] = 3
+    h = ctypes.c_void_p()
+    assert lib.lbm13_create(48, 40, ctypes.byref(params), ctypes.byref(bnd), 0, ctypes.byref(alloc), stream,
+                            ctypes.byref(h)) == 0
+    assert lib.lbm13_step(h, 10) == 0
+    out = np.zeros(16)
+    assert lib.lbm13_residual(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 2
+    budget["n"] = 10
+    assert lib.lbm13_residual(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    assert out[14] == 10 and out[4] == pytest.approx(48 * 40, rel=1e-6)
+    lib.lbm13_destroy(h)
+    assert not live
