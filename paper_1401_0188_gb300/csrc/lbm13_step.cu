@@ -152,6 +152,17 @@ cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s)
     cudaError_t e = launch_walls(a, s);
     if (e != cudaSuccess) return e;
     dim3 block(32, BY);
+    // A lattice of fewer than four R-row tiles per SM is latency-bound: one
+    // row per thread doubles the blocks in flight (same per-node arithmetic).
+    const long long tiles2 = (long long)((a.nx + 31) / 32) * ((a.ny + BY * R - 1) / (BY * R));
+    if (R == 2 && tiles2 < 4 * 152) {
+        dim3 grid1((a.nx + 31) / 32, (a.ny + BY - 1) / BY);
+        if (force)
+            step_kernel<T, C, true, 1><<<grid1, block, 0, s>>>(a);
+        else
+            step_kernel<T, C, false, 1><<<grid1, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     dim3 grid((a.nx + 31) / 32, (a.ny + BY * R - 1) / (BY * R));
     if (force)
         step_kernel<T, C, true, R><<<grid, block, 0, s>>>(a);
