@@ -3,6 +3,7 @@
   python -m paper_1401_0188_gb300.validate cavity  [--L 256] [--Ra 1e3 1e4 1e5] [--tol 1e-8]
   python -m paper_1401_0188_gb300.validate channels [--nx 1024] [--ny 128]
   python -m paper_1401_0188_gb300.validate waves [--precision both]
+  python -m paper_1401_0188_gb300.validate serving [--requests 64 --rate 200 --side-max 512 --ra-max 1e6]
 
 `cavity`: the differentially heated cavity of Sec. 10 in FP64 and in
 FP32-deviation storage, each run until the residual reaches `tol`; prints per
@@ -12,6 +13,9 @@ error against FP64 per result.
 Poiseuille flow of Sec. 8 (body force), compared with their closed forms.
 `waves`: the thermal wave (Sec. 4), buoyancy wave (Sec. 5), transverse-wave
 aggregates (Sec. 6) and heated slab (Sec. 9) against their closed forms.
+`serving`: a Poisson trace of cavity and channel solves served with continuous
+batching (p50/p99 time to steady state, throughput) and the Nusselt numbers of
+its smallest cavities against plain FP64 runs.
 One JSON object per line.
 """
 import argparse
@@ -173,6 +177,29 @@ def run_waves(precisions):
                       flush=True)
 
 
+def run_serving(n, rate, side_min, side_max, ra_min, ra_max, tol, check_every, fp64_subset):
+    """A Poisson trace of cavity and channel requests served with continuous
+    batching (FP32-deviation), then the `fp64_subset` smallest cavity requests
+    again in plain FP64, one lattice per launch, with the same stopping rule:
+    the Nusselt-number difference states the served accuracy."""
+    from . import serving as S
+    reqs = S.poisson_trace(n, rate=rate, seed=5151, side_range=(side_min, side_max), ra_range=(ra_min, ra_max),
+                           tol=tol)
+    srv = S.Server(lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=check_every, realtime=True)
+    res, summary = srv.run(reqs)
+    sides = [r.nx for r in res]
+    print(json.dumps({"case": "serving", "requests": n, "rate_per_s": rate, "sides": [side_min, side_max],
+                      "Ra": [ra_min, ra_max], "tol": tol, **summary,
+                      "max_side_served": max(sides), "steps_max": max(r.steps for r in res)}), flush=True)
+    cav = sorted([r for r in reqs if r.kind == "cavity"], key=lambda r: r.L)[:fp64_subset]
+    base, _ = S.Server(lbm13.FP64, check_every=check_every, batched=False, realtime=False).run(cav)
+    served = {r.rid: r for r in res}
+    errs = [{"rid": b.rid, "L": b.nx, "Ra": b.Ra, "Nu_fp64": b.Nu, "Nu_fp32_served": served[b.rid].Nu,
+             "abs_err": abs(served[b.rid].Nu - b.Nu)} for b in base]
+    print(json.dumps({"case": "serving_nusselt_vs_fp64", "cavities": errs,
+                      "max_abs_err": max(e["abs_err"] for e in errs)}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -189,6 +216,16 @@ def main(argv=None):
     h.add_argument("--steps-factor", type=float, default=3.0)
     w = sub.add_parser("waves")
     w.add_argument("--precision", choices=["fp64", "fp32", "both"], default="both")
+    v = sub.add_parser("serving")
+    v.add_argument("--requests", type=int, default=64)
+    v.add_argument("--rate", type=float, default=200.0)
+    v.add_argument("--side-min", type=int, default=64)
+    v.add_argument("--side-max", type=int, default=512)
+    v.add_argument("--ra-min", type=float, default=1e3)
+    v.add_argument("--ra-max", type=float, default=1e6)
+    v.add_argument("--tol", type=float, default=1e-7)
+    v.add_argument("--check-every", type=int, default=1000)
+    v.add_argument("--fp64-subset", type=int, default=6)
     a = ap.parse_args(argv)
     from . import build
     build.build()
@@ -196,6 +233,9 @@ def main(argv=None):
         run_cavity(a.L, a.Ra, a.Pr, a.tol, a.check_every, a.max_steps)
     elif a.cmd == "channels":
         run_channels(a.nx, a.ny, a.steps_factor)
+    elif a.cmd == "serving":
+        run_serving(a.requests, a.rate, a.side_min, a.side_max, a.ra_min, a.ra_max, a.tol, a.check_every,
+                    a.fp64_subset)
     else:
         precs = {"fp64": [lbm13.FP64], "fp32": [lbm13.FP32_DEVIATION],
                  "both": [lbm13.FP64, lbm13.FP32_DEVIATION]}[a.precision]
