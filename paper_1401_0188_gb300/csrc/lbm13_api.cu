@@ -32,6 +32,7 @@ struct lbm13_lattice {
     Coef<float> kf{};
     WallArgs<double> wd[4]{};
     WallArgs<float> wf[4]{};
+    double corner_poly[4][5] = {};  // corner corrections as polynomials (StepArgs::corner_poly)
     bool force = false;
     // wall corrections written by the boundary-link kernel (when a wall needs data)
     void *corr = nullptr;
@@ -254,21 +255,87 @@ void fill_coef(lbm13_t h, Coef<C> &k)
     k.t9X9 = C(-16.0 * lXX - lXXe);
 }
 
+// Coefficients (a0 .. a4) of P(drho, dE) = a0 + a1 drho + a2 dE + a3 drho^2 +
+// a4 drho dE from values of P, which is exactly of that form: every
+// equilibrium moment at rho = 1 + drho, E = E0 + dE, j = rho u is a
+// combination of rho, E, rho^2 and rho E (Eq. d2q13-moments-equil).  The
+// sample points rho = 1, 1 +- 1/2 and E0, E0 +- 1/2 give the coefficients
+// without truncation error.
+template <typename F>
+void quadratic_coefficients(F P, double a[5])
+{
+    const double h = 0.5;
+    const double p00 = P(0.0, 0.0), pp0 = P(h, 0.0), pm0 = P(-h, 0.0);
+    const double p0p = P(0.0, h), p0m = P(0.0, -h), ppp = P(h, h);
+    a[0] = p00;
+    a[1] = (pp0 - pm0) / (2.0 * h);
+    a[2] = (p0p - p0m) / (2.0 * h);
+    a[3] = (pp0 + pm0 - 2.0 * p00) / (2.0 * h * h);
+    a[4] = (ppp - pp0 - p0p + p00) / (h * h);
+}
+
+// Deviation of the equilibrium populations for the wall state (drho, dE) and
+// wall velocity (ux, uy), from the double coefficients of the lattice.
+void wall_equilibrium(lbm13_t h, double drho, double dE, double ux, double uy, double f[Q])
+{
+    const double rho = 1.0 + drho;
+    equilibrium_dev(drho, dE, rho * ux, rho * uy, h->kd, f);
+}
+
 template <typename C>
 void fill_walls(lbm13_t h, WallArgs<C> *w)
 {
     const lbm13_wall *src[4] = {&h->b.west, &h->b.east, &h->b.south, &h->b.north};
+    double U[4][2];
     for (int s = 0; s < 4; ++s) {
         const lbm13_wall &in = *src[s];
         WallArgs<C> &o = w[s];
+        const double ux = s <= EAST ? 0.0 : in.u_t, uy = s <= EAST ? in.u_t : 0.0;
+        U[s][0] = ux;
+        U[s][1] = uy;
         o.kind = in.kind;
         o.needs_data = in.kind == WALL_MIXED || (in.kind == WALL_BB && in.u_t != 0.0);
-        o.ux = C(s <= EAST ? 0.0 : in.u_t);
-        o.uy = C(s <= EAST ? in.u_t : 0.0);
+        o.ux = C(ux);
+        o.uy = C(uy);
         o.base = C(26.0 * in.T - 28.0);
         o.eT = C(26.0 * (in.T - (h->p.E0 + 28.0) / 26.0));
         o.mass_flux = in.kind == WALL_MIXED && h->b.wall_density == LBM13_WALL_DENSITY_ZERO_FLUX;
         o.wsum = C(h->derived[22 + 1] + 2.0 * h->derived[22 + 9]);
+        // zero-flux density: even parts of the unit-density wall equilibrium on
+        // the outgoing unit and distance-2 normal links
+        double e[Q];
+        wall_equilibrium(h, 0.0, 26.0 * (in.T - (h->p.E0 + 28.0) / 26.0) + 13.0 * (ux * ux + uy * uy), ux, uy, e);
+        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
+        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
+        o.zf_ea = C(0.5 * (e[ja] + e[copp(ja)]));
+        o.zf_eb = C(0.5 * (e[jb] + e[copp(jb)]));
+        for (int i = 0; i < 4; ++i) {
+            const int j = wall_link(s, i), jn = copp(j);
+            const bool normal = s <= EAST ? cvy(j) == 0 : cvx(j) == 0;
+            const bool abb = in.kind == WALL_MIXED && normal;
+            double a[5];
+            quadratic_coefficients(
+                [&](double dr, double de) {
+                    double f[Q];
+                    wall_equilibrium(h, dr, de, ux, uy, f);
+                    return abb ? f[j] + f[jn] : f[j] - f[jn];
+                },
+                a);
+            for (int m = 0; m < 5; ++m) o.poly[i][m] = C(a[m]);
+        }
+    }
+    // corners: bounce-back with the mean of the two walls' states
+    for (int c = 0; c < 4; ++c) {
+        const int sx = (c & 1) ? EAST : WEST, sy = (c & 2) ? NORTH : SOUTH;
+        const double ux = 0.5 * (U[sx][0] + U[sy][0]), uy = 0.5 * (U[sx][1] + U[sy][1]);
+        const int j = corner_link(c), jn = copp(j);
+        quadratic_coefficients(
+            [&](double dr, double de) {
+                double f[Q];
+                wall_equilibrium(h, dr, de, ux, uy, f);
+                return f[j] - f[jn];
+            },
+            h->corner_poly[c]);
     }
 }
 
@@ -308,6 +375,8 @@ StepArgs<T, C> step_args(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C>
     a.plane = h->plane;
     a.k = k;
     for (int s = 0; s < 4; ++s) a.wall[s] = w[s];
+    for (int c = 0; c < 4; ++c)
+        for (int m = 0; m < 5; ++m) a.corner_poly[c][m] = C(h->corner_poly[c][m]);
     return a;
 }
 

@@ -25,6 +25,13 @@ struct WallArgs {
     C eT;            // 26 T_w - 28 - E0 = 26 (T_w - T0)
     int mass_flux;   // temperature wall whose density makes the net normal mass flux zero
     C wsum;          // w_unit + 2 w_two: rest populations of one unit and one distance-2 axis link
+    C zf_ea, zf_eb;  // zero-flux density: even parts of the wall equilibrium at unit density,
+                     // unit and distance-2 normal links
+    // The correction of each entering link (slot i) as an exact polynomial in
+    // the wall state's deviations (drho, dE): poly[i] = (a0, a1, a2, a3, a4) of
+    // a0 + a1 drho + a2 dE + a3 drho^2 + a4 drho dE (every equilibrium moment
+    // is at most quadratic in rho and E once j = rho u).
+    C poly[4][5];
 };
 
 // Links that enter the lattice across each side, four per side, in a fixed
@@ -59,6 +66,9 @@ struct alignas(16) StepArgs {
     C *corr;
     int corr_stride;  // max(nx, ny)
     int any_wall_data;
+    // corner c's bounce-back correction as a polynomial in the mean of the two
+    // walls' (drho, dE), with the mean wall velocity (same form as WallArgs::poly)
+    C corner_poly[4][5];
     int nx, ny;
     int per_x, per_y;
     long long pitch;  // elements per row

@@ -28,9 +28,9 @@ __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
 
 // ------------------------------------------------------ boundary links
 
-// Wall state at position `pos` along side `s`: st = (drho_w, dE_w, ux_w, uy_w).
+// Wall state at position `pos` along side `s`: st = (drho_w, dE_w).
 template <typename T, typename C>
-__device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[4])
+__device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[2])
 {
     const WallArgs<C> &w = a.wall[s];
     int x0, y0, x1, y1;
@@ -49,14 +49,12 @@ __device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[4])
         // every even moment of the wall equilibrium is proportional to rho_w,
         // so the anti-bounce-back links return 2 rho_w e_j; rho_w balances the
         // outgoing normal populations (unit link from the first node, the
-        // distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two)
+        // distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two),
+        // e the even parts at unit density (zf_ea, zf_eb)
         const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
         const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
-        C e[Q];
-        equilibrium_dev(C(0), w.eT + C(13) * (w.ux * w.ux + w.uy * w.uy), w.ux, w.uy, a.k, e);
-        const C ea = C(0.5) * (e[ja] + e[copp(ja)]), eb = C(0.5) * (e[jb] + e[copp(jb)]);
         const C dout = g0[ja] + g0[jb] + g1[jb];
-        drho = (dout - ea - C(2) * eb) / (w.wsum + ea + C(2) * eb);
+        drho = (dout - w.zf_ea - C(2) * w.zf_eb) / (w.wsum + w.zf_ea + C(2) * w.zf_eb);
     } else {
         drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
     }
@@ -68,50 +66,43 @@ __device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[4])
         dE = C(1.5) * energy_dev(g0) - C(0.5) * energy_dev(g1);
     st[0] = drho;
     st[1] = dE;
-    st[2] = w.ux;
-    st[3] = w.uy;
 }
 
+// a0 + a1 x + a2 y + a3 x^2 + a4 x y (a wall correction from the wall state).
 template <typename C>
-__device__ __forceinline__ void wall_feq(const Coef<C> &k, const C st[4], C feq[Q])
+__device__ __forceinline__ C wall_poly(const C p[5], C x, C y)
 {
-    const C rho = C(1) + st[0];
-    equilibrium_dev(st[0], st[1], rho * st[2], rho * st[3], k, feq);
+    return p[0] + x * (p[1] + x * p[3] + y * p[4]) + y * p[2];
 }
 
 // One wall position (or corner) of one lattice: items below 2 ny are the
 // west/east positions, then 2 nx south/north positions, then the 4 corners.
+// The corrections (2 f_eq,odd of the entering link for bounce-back, 2
+// f_eq,even for anti-bounce-back, at the wall state) are evaluated from their
+// exact quadratic form in the wall state's (drho, dE).
 template <typename T, typename C>
 __device__ void wall_item(const StepArgs<T, C> &a, int item)
 {
     const int nx = a.nx, ny = a.ny;
-    C st[4], feq[Q];
+    C st[2];
     if (item < 2 * ny + 2 * nx) {
         const int s = item < 2 * ny ? (item < ny ? WEST : EAST) : (item - 2 * ny < nx ? SOUTH : NORTH);
         const int pos = item < 2 * ny ? item % ny : (item - 2 * ny) % nx;
         const WallArgs<C> &w = a.wall[s];
         if (w.kind == PERIODIC || !w.needs_data) return;
         wall_state(a, s, pos, st);
-        wall_feq(a.k, st, feq);
         C *out = a.corr + ((long long)s * a.corr_stride + pos) * 4;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int j = wall_link(s, i), jb = copp(j);
-            const bool normal = s <= EAST ? cvy(j) == 0 : cvx(j) == 0;
-            out[i] = (w.kind == WALL_MIXED && normal) ? feq[j] + feq[jb] : feq[j] - feq[jb];
-        }
+        for (int i = 0; i < 4; ++i) out[i] = wall_poly(w.poly[i], st[0], st[1]);
     } else if (item < 2 * ny + 2 * nx + 4) {
         const int c = item - 2 * ny - 2 * nx;
         const int sx = (c & 1) ? EAST : WEST, sy = (c & 2) ? NORTH : SOUTH;
         if (a.per_x || a.per_y || !(a.wall[sx].needs_data || a.wall[sy].needs_data)) return;
-        C s1[4], s2[4];
+        C s1[2], s2[2];
         wall_state(a, sx, (c & 2) ? ny - 1 : 0, s1);
         wall_state(a, sy, (c & 1) ? nx - 1 : 0, s2);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) st[i] = C(0.5) * (s1[i] + s2[i]);
-        wall_feq(a.k, st, feq);
-        const int j = corner_link(c);
-        a.corr[16LL * a.corr_stride + c] = feq[j] - feq[copp(j)];
+        a.corr[16LL * a.corr_stride + c] =
+            wall_poly(a.corner_poly[c], C(0.5) * (s1[0] + s2[0]), C(0.5) * (s1[1] + s2[1]));
     }
 }
 
