@@ -34,10 +34,6 @@ struct lbm13_lattice {
     WallArgs<float> wf[4]{};
     double corner_poly[4][5] = {};  // corner corrections as polynomials (StepArgs::corner_poly)
     bool force = false;
-    // wall corrections written by the boundary-link kernel (when a wall needs data)
-    void *corr = nullptr;
-    size_t corr_bytes = 0;
-    bool any_wall_data = false;
     // CUDA graphs of kGraphSteps steps, one per starting buffer parity
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -364,9 +360,6 @@ StepArgs<T, C> step_args(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C>
     StepArgs<T, C> a{};
     a.fin = static_cast<const T *>(h->buf[cur]);
     a.fout = static_cast<T *>(h->buf[cur ^ 1]);
-    a.corr = static_cast<C *>(h->corr);
-    a.corr_stride = h->nx > h->ny ? h->nx : h->ny;
-    a.any_wall_data = h->any_wall_data ? 1 : 0;
     a.nx = h->nx;
     a.ny = h->ny;
     a.per_x = h->b.west.kind == PERIODIC;
@@ -632,20 +625,6 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
             return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the population buffers");
         }
     }
-    for (int s = 0; s < 4; ++s) h->any_wall_data = h->any_wall_data || h->wd[s].needs_data;
-    if (h->any_wall_data) {
-        h->corr_bytes = size_t(corr_count(nx, ny)) * h->elem;
-        h->corr = dev_alloc(h, h->corr_bytes);
-        if (!h->corr) {
-            lbm13_destroy(h);
-            return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the wall corrections");
-        }
-        cudaError_t e = cudaMemsetAsync(h->corr, 0, h->corr_bytes, h->stream);
-        if (e != cudaSuccess) {
-            lbm13_destroy(h);
-            return cuda_fail(nullptr, e, "cudaMemsetAsync (wall corrections)");
-        }
-    }
     // deviation 0 everywhere = the rest state rho = 1, u = 0, T = T0
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = cudaMemsetAsync(h->buf[i], 0, h->state_bytes, h->stream);
@@ -667,7 +646,6 @@ void lbm13_destroy(lbm13_t h)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (int i = 0; i < 2; ++i) dev_free(h, h->buf[i], h->state_bytes);
-    dev_free(h, h->corr, h->corr_bytes);
     if (h->red_mem) {
         const long long n = (long long)h->nx * h->ny;
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));
@@ -989,9 +967,6 @@ struct lbm13_plan {
     size_t work_bytes = 0;
     int ntiles = 0;
     double *res_dev = nullptr;  // [count][16] results of lbm13_plan_residual
-    void *wlats = nullptr;  // (lattice, first wall item) per block of the boundary-link launch
-    size_t wlats_bytes = 0;
-    int nwlats = 0;
     long long nodes = 0;
     std::vector<int> cur0;
     int parity = 0;  // parity of the next launch relative to cur0
@@ -1051,27 +1026,6 @@ int plan_upload_descs(lbm13_plan_t p)
         host[i].force = h->force ? 1 : 0;
         host[i].tiles_x = (h->nx + 31) / 32;
         p->cur0[i] = h->cur;
-    }
-    // boundary-link work: one block of kWallBlock items per entry, so that the
-    // wall positions of a large lattice are spread over many blocks
-    std::vector<int2> wl;
-    for (size_t i = 0; i < p->lats.size(); ++i) {
-        lbm13_t h = p->lats[i];
-        if (!h->any_wall_data) continue;
-        const int items = 2 * (h->nx + h->ny) + 4;
-        for (int b = 0; b < items; b += kWallBlock) wl.push_back(make_int2(int(i), b));
-    }
-    p->nwlats = int(wl.size());
-    if (!wl.empty()) {
-        const size_t wb = wl.size() * sizeof(int2);
-        if (!p->wlats || p->wlats_bytes < wb) {
-            plan_free(p, p->wlats);
-            p->wlats = plan_alloc(p, wb);
-            p->wlats_bytes = wb;
-            if (!p->wlats) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the wall list");
-        }
-        cudaError_t e = cudaMemcpyAsync(p->wlats, wl.data(), wb, cudaMemcpyHostToDevice, p->stream);
-        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("wall list upload: ") + cudaGetErrorString(e));
     }
     const size_t bytes = host.size() * sizeof(BatchDesc<T, C>);
     if (!p->desc || p->desc_bytes < bytes) {
@@ -1137,17 +1091,12 @@ int plan_build_work(lbm13_plan_t p)
 
 cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
 {
-    cudaError_t e;
     if (p->precision == LBM13_FP64) {
         const auto *d = static_cast<const BatchDesc<double, double> *>(p->desc);
-        e = launch_batch_walls<double, double>(d, static_cast<const int2 *>(p->wlats), p->nwlats, parity, s);
-        if (e != cudaSuccess) return e;
         return launch_batch<double, double>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
                                             p->groups, p->grid, s);
     }
     const auto *d = static_cast<const BatchDesc<float, float> *>(p->desc);
-    e = launch_batch_walls<float, float>(d, static_cast<const int2 *>(p->wlats), p->nwlats, parity, s);
-    if (e != cudaSuccess) return e;
     return launch_batch<float, float>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
                                       p->groups, p->grid, s);
 }
@@ -1257,7 +1206,6 @@ void lbm13_plan_destroy(lbm13_plan_t p)
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     plan_free(p, p->desc);
     plan_free(p, p->work);
-    plan_free(p, p->wlats);
     plan_free(p, p->res_dev);
     delete p;
 }

@@ -57,15 +57,6 @@ template <typename T, typename C>
 struct alignas(16) StepArgs {
     const T *__restrict__ fin;
     T *__restrict__ fout;
-    // Wall corrections, written by the boundary-link kernel before each step:
-    // corr[(side * corr_stride + pos) * 4 + slot] is the term added to the
-    // reflected population of the link in `slot` at position `pos` along the
-    // side (2 f_eq,odd for bounce-back, 2 f_eq,even for anti-bounce-back), and
-    // corr[16 * corr_stride + c] that of corner c.  Only sides that need wall
-    // data (temperature walls, moving walls) are written and read.
-    C *corr;
-    int corr_stride;  // max(nx, ny)
-    int any_wall_data;
     // corner c's bounce-back correction as a polynomial in the mean of the two
     // walls' (drho, dE), with the mean wall velocity (same form as WallArgs::poly)
     C corner_poly[4][5];
@@ -133,19 +124,6 @@ struct ReadArgs {
 // Launchers (return the cudaError_t of the launch).
 template <typename T, typename C>
 cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s);
-
-// Doubles/floats of wall corrections for an nx x ny lattice.
-inline long long corr_count(int nx, int ny) { return 16LL * (nx > ny ? nx : ny) + 4; }
-
-// Boundary-link kernel of one lattice (no-op when no wall needs data).
-template <typename T, typename C>
-cudaError_t launch_walls(const StepArgs<T, C> &a, cudaStream_t s);
-
-// Boundary-link kernel of a batch: one block of kWallBlock threads per work
-// entry (lattice, first wall item), each thread one wall item.
-constexpr int kWallBlock = 128;
-template <typename T, typename C>
-cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int2 *work, int nwork, int parity, cudaStream_t s);
 
 // Tile shapes (rows per thread R, warps per block BY) of the batched kernel.
 bool batch_shape_supported(int R, int BY);

@@ -4,11 +4,10 @@
 // A small lattice (both population buffers well inside the 129 MB L2) is
 // bound by launch latency, not by HBM: a step is a few microseconds of work.
 // Here every block of a co-resident grid takes tiles of the lattice in turn,
-// and a grid barrier separates the phases of a step: the boundary-link
-// corrections (when a wall needs data), then the fused pull + collide + store;
-// the next step reads what the other blocks wrote, so populations and
-// corrections are loaded L2-coherently (__ldcg) instead of through the
-// read-only path.  The per-node arithmetic is the shared device code of the
+// and a grid barrier separates consecutive steps (each fused pull + collide +
+// store, with the wall corrections evaluated by the edge nodes); the next step
+// reads what the other blocks wrote, so populations are loaded L2-coherently
+// (__ldcg) instead of through the read-only path.  The per-node arithmetic is the shared device code of the
 // per-step kernels, so the results are bit-identical to stepping launch by
 // launch.
 //
@@ -81,12 +80,6 @@ template <typename T, typename C, bool Force, int R>
 __device__ __forceinline__ bool grid_step(const StepArgs<T, C> &a, int tiles_x, int ntiles, bool last, C *slot,
                                           const GridSync &g)
 {
-    if (a.any_wall_data) {
-        const int items = 2 * (a.nx + a.ny) + 4;
-        const int tid = threadIdx.y * 32 + threadIdx.x;
-        for (int i = blockIdx.x * 128 + tid; i < items; i += gridDim.x * 128) wall_item(a, i);
-        if (!grid_barrier(g, gridDim.x)) return false;
-    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = t % tiles_x, ty = t / tiles_x;
         process_column<T, C, Force, R>(a, tx * 32 + threadIdx.x, (ty * 4 + threadIdx.y) * R, slot);

@@ -39,22 +39,6 @@ namespace lbm13 {
 
 namespace {
 
-template <typename T, typename C>
-__global__ void __launch_bounds__(128) wall_kernel(const StepArgs<T, C> a)
-{
-    wall_item(a, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-template <typename T, typename C>
-__global__ void __launch_bounds__(kWallBlock) batch_wall_kernel(const BatchDesc<T, C> *__restrict__ descs,
-                                                               const int2 *__restrict__ work, int parity)
-{
-    const int2 w = work[blockIdx.x];
-    const StepArgs<T, C> &a = descs[w.x].a[parity];
-    const int item = w.y + int(threadIdx.x);
-    if (item < 2 * (a.nx + a.ny) + 4) wall_item(a, item);
-}
-
 // One lattice: block 32 x 4 threads, each thread R rows of one column.
 template <typename T, typename C, bool Force, int R>
 __global__ void __launch_bounds__(128) step_kernel(const StepArgs<T, C> a)
@@ -128,29 +112,10 @@ cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int 
 } // namespace
 
 template <typename T, typename C>
-cudaError_t launch_walls(const StepArgs<T, C> &a, cudaStream_t s)
-{
-    if (!a.any_wall_data) return cudaSuccess;
-    const int items = 2 * (a.nx + a.ny) + 4;
-    wall_kernel<T, C><<<(items + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T, typename C>
-cudaError_t launch_batch_walls(const BatchDesc<T, C> *descs, const int2 *work, int nwork, int parity, cudaStream_t s)
-{
-    if (nwork <= 0) return cudaSuccess;
-    batch_wall_kernel<T, C><<<nwork, kWallBlock, 0, s>>>(descs, work, parity);
-    return cudaGetLastError();
-}
-
-template <typename T, typename C>
 cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s)
 {
     constexpr int R = sizeof(T) == 8 ? 1 : 2;
     constexpr int BY = 4;
-    cudaError_t e = launch_walls(a, s);
-    if (e != cudaSuccess) return e;
     dim3 block(32, BY);
     // A lattice of fewer than four R-row tiles per SM is latency-bound: one
     // row per thread doubles the blocks in flight (same per-node arithmetic).
@@ -191,12 +156,6 @@ cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int nti
     return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_walls<double, double>(const StepArgs<double, double> &, cudaStream_t);
-template cudaError_t launch_walls<float, float>(const StepArgs<float, float> &, cudaStream_t);
-template cudaError_t launch_batch_walls<double, double>(const BatchDesc<double, double> *, const int2 *, int, int,
-                                                        cudaStream_t);
-template cudaError_t launch_batch_walls<float, float>(const BatchDesc<float, float> *, const int2 *, int, int,
-                                                      cudaStream_t);
 template cudaError_t launch_step<double, double>(const StepArgs<double, double> &, bool, cudaStream_t);
 template cudaError_t launch_step<float, float>(const StepArgs<float, float> &, bool, cudaStream_t);
 template cudaError_t launch_batch<double, double>(const BatchDesc<double, double> *, const int2 *, int, int, int, int,

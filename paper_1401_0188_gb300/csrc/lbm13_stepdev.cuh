@@ -28,9 +28,10 @@ __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
 
 // ------------------------------------------------------ boundary links
 
-// Wall state at position `pos` along side `s`: st = (drho_w, dE_w).
+// Wall state at position `pos` along side `s`: st = (drho_w, dE_w).  Out of
+// line: only the nodes next to a wall that needs data evaluate it.
 template <typename T, typename C>
-__device__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[2])
+__device__ __noinline__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[2])
 {
     const WallArgs<C> &w = a.wall[s];
     int x0, y0, x1, y1;
@@ -75,47 +76,16 @@ __device__ __forceinline__ C wall_poly(const C p[5], C x, C y)
     return p[0] + x * (p[1] + x * p[3] + y * p[4]) + y * p[2];
 }
 
-// One wall position (or corner) of one lattice: items below 2 ny are the
-// west/east positions, then 2 nx south/north positions, then the 4 corners.
-// The corrections (2 f_eq,odd of the entering link for bounce-back, 2
-// f_eq,even for anti-bounce-back, at the wall state) are evaluated from their
-// exact quadratic form in the wall state's (drho, dE).
+// Value of link j of node (x, y) whose source lies beyond side `side` only;
+// st is that side's wall state at the node's position (used when the wall
+// needs data).
 template <typename T, typename C>
-__device__ void wall_item(const StepArgs<T, C> &a, int item)
-{
-    const int nx = a.nx, ny = a.ny;
-    C st[2];
-    if (item < 2 * ny + 2 * nx) {
-        const int s = item < 2 * ny ? (item < ny ? WEST : EAST) : (item - 2 * ny < nx ? SOUTH : NORTH);
-        const int pos = item < 2 * ny ? item % ny : (item - 2 * ny) % nx;
-        const WallArgs<C> &w = a.wall[s];
-        if (w.kind == PERIODIC || !w.needs_data) return;
-        wall_state(a, s, pos, st);
-        C *out = a.corr + ((long long)s * a.corr_stride + pos) * 4;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) out[i] = wall_poly(w.poly[i], st[0], st[1]);
-    } else if (item < 2 * ny + 2 * nx + 4) {
-        const int c = item - 2 * ny - 2 * nx;
-        const int sx = (c & 1) ? EAST : WEST, sy = (c & 2) ? NORTH : SOUTH;
-        if (a.per_x || a.per_y || !(a.wall[sx].needs_data || a.wall[sy].needs_data)) return;
-        C s1[2], s2[2];
-        wall_state(a, sx, (c & 2) ? ny - 1 : 0, s1);
-        wall_state(a, sy, (c & 1) ? nx - 1 : 0, s2);
-        a.corr[16LL * a.corr_stride + c] =
-            wall_poly(a.corner_poly[c], C(0.5) * (s1[0] + s2[0]), C(0.5) * (s1[1] + s2[1]));
-    }
-}
-
-// Value of link j of node (x, y) whose source lies beyond side `side` only.
-template <typename T, typename C>
-__device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j, int x, int y)
+__device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j, int x, int y, const C st[2])
 {
     const int jb = copp(j);
     const WallArgs<C> &w = a.wall[side];
     const bool xwall = side <= EAST;
-    const int pos = xwall ? y : x;
-    const C add = w.needs_data ? LBM13_LDG(a.corr + ((long long)side * a.corr_stride + pos) * 4 + wall_slot(side, j))
-                               : C(0);
+    const C add = w.needs_data ? wall_poly(w.poly[wall_slot(side, j)], st[0], st[1]) : C(0);
     const bool normal = xwall ? cvy(j) == 0 : cvx(j) == 0;
     if (!normal) return ld(a, jb, x, y) + add;
     int xf = x, yf = y;
@@ -129,22 +99,24 @@ __device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j
 template <typename T, typename C>
 __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int y, C f[Q])
 {
-    // Branch-free: every link's source offset, sign and correction are chosen
-    // with selects, so the 13 population loads (and the corrections) are
-    // independent and in flight together.
+    // Branch-free: every link's source offset and sign are chosen with
+    // selects, so the 13 population loads are independent and in flight
+    // together.
     const int nx = a.nx, ny = a.ny;
     const bool px = a.per_x != 0, py = a.per_y != 0;
     const bool west = x <= 1, south = y <= 1;
-    const int kind_x = west ? a.wall[WEST].kind : a.wall[EAST].kind;
-    const int kind_y = south ? a.wall[SOUTH].kind : a.wall[NORTH].kind;
-    const bool nd_x = (west ? a.wall[WEST].needs_data : a.wall[EAST].needs_data) != 0;
-    const bool nd_y = (south ? a.wall[SOUTH].needs_data : a.wall[NORTH].needs_data) != 0;
-    const long long st = a.corr_stride;
-    const long long row_x = ((long long)(west ? WEST : EAST) * st + y) * 4;
-    const long long row_y = ((long long)(south ? SOUTH : NORTH) * st + x) * 4;
-    const long long corner = 16LL * st + (west ? 0 : 1) + (south ? 0 : 2);
-    C v[Q], ad[Q];
-    unsigned cross = 0u, neg = 0u;
+    const int sx_side = west ? WEST : EAST, sy_side = south ? SOUTH : NORTH;
+    const int kind_x = a.wall[sx_side].kind, kind_y = a.wall[sy_side].kind;
+    const bool nd_x = a.wall[sx_side].needs_data != 0, nd_y = a.wall[sy_side].needs_data != 0;
+    // the wall states at this node's position (a corner node's are the
+    // corner's: its x wall at its row, its y wall at its column), before the
+    // pulls so that they are not live across the calls
+    const bool near_x = !px && (x <= 1 || x >= nx - 2), near_y = !py && (y <= 1 || y >= ny - 2);
+    C stx[2] = {C(0), C(0)}, sty[2] = {C(0), C(0)};
+    if (near_x && (nd_x || nd_y)) wall_state(a, sx_side, y, stx);
+    if (near_y && (nd_x || nd_y)) wall_state(a, sy_side, x, sty);
+    C v[Q];
+    unsigned cross = 0u, neg = 0u, crx = 0u, cry = 0u;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         int sx = x - cvx(j), sy = y - cvy(j);
@@ -152,26 +124,35 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
         const bool ox = bx && !px, oy = by && !py;
         sx += sx < 0 ? nx : (sx >= nx ? -nx : 0);
         sy += sy < 0 ? ny : (sy >= ny ? -ny : 0);
-        const bool c = ox || oy, both = ox && oy;
+        const bool c = ox || oy;
         int xs = c ? x : sx, ys = c ? y : sy;
         if (cvy(j) == 0 && (cvx(j) == 2 || cvx(j) == -2) && ox) xs = west ? 1 - x : 2 * nx - 3 - x;
         if (cvx(j) == 0 && (cvy(j) == 2 || cvy(j) == -2) && oy) ys = south ? 1 - y : 2 * ny - 3 - y;
         const int js = c ? copp(j) : j;
         const bool n = (ox && !oy && cvy(j) == 0 && kind_x == WALL_MIXED) ||
                        (oy && !ox && cvx(j) == 0 && kind_y == WALL_MIXED);
-        const bool has = both ? (nd_x || nd_y) : (ox ? nd_x : (oy ? nd_y : false));
-        const int slot_x = west ? wall_slot(WEST, j) : wall_slot(EAST, j);
-        const int slot_y = south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j);
-        const long long coff = both ? corner : (ox ? row_x + slot_x : row_y + slot_y);
         v[j] = C(LBM13_LDG(a.fin + (long long)js * a.plane + (long long)ys * a.pitch + xs));
-        ad[j] = has ? C(LBM13_LDG(a.corr + coff)) : C(0);
         cross |= (c ? 1u : 0u) << j;
         neg |= (n ? 1u : 0u) << j;
+        crx |= (ox ? 1u : 0u) << j;
+        cry |= (oy ? 1u : 0u) << j;
     }
+    const int corner = (west ? 0 : 1) + (south ? 0 : 2);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
+        const bool ox = (crx >> j) & 1u, oy = (cry >> j) & 1u;
+        C ad = C(0);
+        if (ox && oy) {
+            if (nd_x || nd_y)
+                ad = wall_poly(a.corner_poly[corner], C(0.5) * (stx[0] + sty[0]), C(0.5) * (stx[1] + sty[1]));
+        } else if (ox) {
+            if (nd_x) ad = wall_poly(a.wall[sx_side].poly[west ? wall_slot(WEST, j) : wall_slot(EAST, j)], stx[0], stx[1]);
+        } else if (oy) {
+            if (nd_y)
+                ad = wall_poly(a.wall[sy_side].poly[south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j)], sty[0], sty[1]);
+        }
         const C w = ((neg >> j) & 1u) ? -v[j] : v[j];
-        f[j] = ((cross >> j) & 1u) ? w + ad[j] : v[j];
+        f[j] = ((cross >> j) & 1u) ? w + ad : v[j];
     }
 }
 
@@ -190,7 +171,7 @@ __device__ __forceinline__ void store(const StepArgs<T, C> &a, int x, int y, con
 // pulls with the source column clamped into the lattice (uniform code, always
 // in bounds); lanes within two columns of the left or right edge then replace
 // the links that cross that edge (periodic wrap, or the wall rule with the
-// precomputed correction).  Warps on the bottom or top rows resolve every node
+// correction evaluated from the wall state at the node's row).  Warps on the bottom or top rows resolve every node
 // with gather_general through `slot`, this thread's shared-memory row.
 template <typename T, typename C, bool Force, int R>
 __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, int y0, C *slot)
@@ -198,6 +179,17 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
     const int nx = a.nx, ny = a.ny;
     const bool yin = y0 >= 2 && y0 + R <= ny - 2;
     if (__all_sync(0xffffffffu, yin)) {
+        // lanes next to an x wall that needs data evaluate its state at their
+        // rows first (nothing else is live yet)
+        const bool xedge = x < nx && (x < 2 || x >= nx - 2) && !a.per_x;
+        const int side = x < 2 ? WEST : EAST;
+        C st[R][2];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            st[r][0] = C(0);
+            st[r][1] = C(0);
+            if (xedge && a.wall[side].needs_data) wall_state(a, side, y0 + r, st[r]);
+        }
         C f[R][Q];
         const T *base = a.fin + (long long)y0 * a.pitch;
 #pragma unroll
@@ -220,7 +212,7 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
                     if (a.per_x)
                         f[r][j] = ld(a, j, sx < 0 ? sx + nx : sx - nx, y0 + r - cvy(j));
                     else
-                        f[r][j] = cross_wall(a, sx < 0 ? WEST : EAST, j, x, y0 + r);
+                        f[r][j] = cross_wall(a, side, j, x, y0 + r, st[r]);
                 }
             }
         }

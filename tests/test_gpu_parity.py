@@ -334,7 +334,7 @@ def test_full_size_sampled_nodes_match_oracle(L, pstar, n, prec, steps):
 
 def test_allocator_failure_is_reported(L, pstar):
     """Injected on the host: a caller allocator that returns NULL.  Creation
-    fails with LBM13_ENOMEM when a population or wall buffer cannot be had; a
+    fails with LBM13_ENOMEM when a population buffer cannot be had; a
     lattice whose first read-out cannot get its reduction buffers reports
     LBM13_ENOMEM, keeps its state, and works once memory is available again."""
     import ctypes
@@ -362,14 +362,14 @@ def test_allocator_failure_is_reported(L, pstar):
     params = L.make_params(pstar)
     bnd = L.make_boundary(W.cavity(T0, 0.01, 2e-4))
     stream = ctypes.c_void_p(torch.cuda.current_stream(0).cuda_stream)
-    for n in (0, 1, 2):   # buffer 0, buffer 1, wall corrections
+    for n in (0, 1):   # buffer 0, buffer 1
         budget["n"] = n
         h = ctypes.c_void_p()
         st = lib.lbm13_create(48, 40, ctypes.byref(params), ctypes.byref(bnd), 0, ctypes.byref(alloc), stream,
                               ctypes.byref(h))
         assert st == 2 and not h.value, (n, st)
         assert not live
-    budget["n"] = 3
+    budget["n"] = 2
     h = ctypes.c_void_p()
     assert lib.lbm13_create(48, 40, ctypes.byref(params), ctypes.byref(bnd), 0, ctypes.byref(alloc), stream,
                             ctypes.byref(h)) == 0
