@@ -39,9 +39,12 @@ namespace lbm13 {
 
 namespace {
 
-// One lattice: block 32 x 4 threads, each thread R rows of one column.
+// One lattice: block 32 x 4 threads, each thread R rows of one column.  The
+// register caps keep 6 blocks (24 warps) per SM for FP32 and 5 for FP64 and
+// the forced two-row FP32 variant, without spills: more warps keep more
+// population loads in flight.
 template <typename T, typename C, bool Force, int R>
-__global__ void __launch_bounds__(128) step_kernel(const StepArgs<T, C> a)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 && !(Force && R == 2) ? 6 : 5) step_kernel(const StepArgs<T, C> a)
 {
     __shared__ C slots[128][Q];
     const int tid = threadIdx.y * 32 + threadIdx.x;

@@ -28,10 +28,18 @@ __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
 
 // ------------------------------------------------------ boundary links
 
-// Wall state at position `pos` along side `s`: st = (drho_w, dE_w).  Out of
-// line: only the nodes next to a wall that needs data evaluate it.
+// Wall state (drho_w, dE_w): deviations of the wall's density and energy from
+// the rest state.
+template <typename C>
+struct WallState {
+    C rho, E;
+};
+
+// Wall state at position `pos` along side `s`.  Out of line: only the nodes
+// next to a wall that needs data evaluate it; returned by value so that the
+// caller keeps it in registers (no stack frame).
 template <typename T, typename C>
-__device__ __noinline__ void wall_state(const StepArgs<T, C> &a, int s, int pos, C st[2])
+__device__ __noinline__ WallState<C> wall_state(const StepArgs<T, C> &a, int s, int pos)
 {
     const WallArgs<C> &w = a.wall[s];
     int x0, y0, x1, y1;
@@ -65,8 +73,7 @@ __device__ __noinline__ void wall_state(const StepArgs<T, C> &a, int s, int pos,
         dE = drho * w.base + w.eT + C(13) * rho * (w.ux * w.ux + w.uy * w.uy);
     else
         dE = C(1.5) * energy_dev(g0) - C(0.5) * energy_dev(g1);
-    st[0] = drho;
-    st[1] = dE;
+    return {drho, dE};
 }
 
 // a0 + a1 x + a2 y + a3 x^2 + a4 x y (a wall correction from the wall state).
@@ -80,12 +87,12 @@ __device__ __forceinline__ C wall_poly(const C p[5], C x, C y)
 // st is that side's wall state at the node's position (used when the wall
 // needs data).
 template <typename T, typename C>
-__device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j, int x, int y, const C st[2])
+__device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j, int x, int y, WallState<C> st)
 {
     const int jb = copp(j);
     const WallArgs<C> &w = a.wall[side];
     const bool xwall = side <= EAST;
-    const C add = w.needs_data ? wall_poly(w.poly[wall_slot(side, j)], st[0], st[1]) : C(0);
+    const C add = w.needs_data ? wall_poly(w.poly[wall_slot(side, j)], st.rho, st.E) : C(0);
     const bool normal = xwall ? cvy(j) == 0 : cvx(j) == 0;
     if (!normal) return ld(a, jb, x, y) + add;
     int xf = x, yf = y;
@@ -112,9 +119,9 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
     // corner's: its x wall at its row, its y wall at its column), before the
     // pulls so that they are not live across the calls
     const bool near_x = !px && (x <= 1 || x >= nx - 2), near_y = !py && (y <= 1 || y >= ny - 2);
-    C stx[2] = {C(0), C(0)}, sty[2] = {C(0), C(0)};
-    if (near_x && (nd_x || nd_y)) wall_state(a, sx_side, y, stx);
-    if (near_y && (nd_x || nd_y)) wall_state(a, sy_side, x, sty);
+    WallState<C> stx = {C(0), C(0)}, sty = {C(0), C(0)};
+    if (near_x && (nd_x || nd_y)) stx = wall_state(a, sx_side, y);
+    if (near_y && (nd_x || nd_y)) sty = wall_state(a, sy_side, x);
     C v[Q];
     unsigned cross = 0u, neg = 0u, crx = 0u, cry = 0u;
 #pragma unroll
@@ -144,12 +151,12 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
         C ad = C(0);
         if (ox && oy) {
             if (nd_x || nd_y)
-                ad = wall_poly(a.corner_poly[corner], C(0.5) * (stx[0] + sty[0]), C(0.5) * (stx[1] + sty[1]));
+                ad = wall_poly(a.corner_poly[corner], C(0.5) * (stx.rho + sty.rho), C(0.5) * (stx.E + sty.E));
         } else if (ox) {
-            if (nd_x) ad = wall_poly(a.wall[sx_side].poly[west ? wall_slot(WEST, j) : wall_slot(EAST, j)], stx[0], stx[1]);
+            if (nd_x) ad = wall_poly(a.wall[sx_side].poly[west ? wall_slot(WEST, j) : wall_slot(EAST, j)], stx.rho, stx.E);
         } else if (oy) {
             if (nd_y)
-                ad = wall_poly(a.wall[sy_side].poly[south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j)], sty[0], sty[1]);
+                ad = wall_poly(a.wall[sy_side].poly[south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j)], sty.rho, sty.E);
         }
         const C w = ((neg >> j) & 1u) ? -v[j] : v[j];
         f[j] = ((cross >> j) & 1u) ? w + ad : v[j];
@@ -183,12 +190,11 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
         // rows first (nothing else is live yet)
         const bool xedge = x < nx && (x < 2 || x >= nx - 2) && !a.per_x;
         const int side = x < 2 ? WEST : EAST;
-        C st[R][2];
+        WallState<C> st[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            st[r][0] = C(0);
-            st[r][1] = C(0);
-            if (xedge && a.wall[side].needs_data) wall_state(a, side, y0 + r, st[r]);
+            st[r] = {C(0), C(0)};
+            if (xedge && a.wall[side].needs_data) st[r] = wall_state(a, side, y0 + r);
         }
         C f[R][Q];
         const T *base = a.fin + (long long)y0 * a.pitch;
