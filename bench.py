@@ -274,7 +274,7 @@ def run_batched(args, torch):
             e1.synchronize()
             ms = e0.elapsed_time(e1) / args.batched_steps
             out["tune"] = plan.config()
-            out["gpu_launches_per_step"] = 2
+            out["gpu_launches_per_step"] = 1
             plan.close()
         else:
             steps = max(4, args.batched_steps // 20)

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm13.so")
-SOURCES = ["lbm13_step.cu", "lbm13_multi.cu", "lbm13_aux.cu", "lbm13_api.cu", "lbm13_noalloc.cu", "lbm13_linear.cu"]
+SOURCES = ["lbm13_step.cu", "lbm13_batch.cu", "lbm13_multi.cu", "lbm13_aux.cu", "lbm13_api.cu", "lbm13_noalloc.cu", "lbm13_linear.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
