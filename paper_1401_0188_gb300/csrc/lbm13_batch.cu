@@ -22,10 +22,11 @@ namespace {
 // work item is fetched while the current one runs.  The block copies a
 // lattice's arguments for this step's buffer parity into shared memory with
 // 16-byte loads spread over its threads, only when the lattice changes.
-// One row per thread keeps to 64 registers (half the SM's warps resident);
-// more rows per thread take what they need.
+// One row per thread keeps to 64 registers (half the SM's warps resident),
+// two rows to 80 (24 warps: as many loads in flight as the one-lattice
+// kernel); more rows per thread take what they need.
 template <typename T, typename C, int R, int BY>
-__global__ void __launch_bounds__(32 * BY, (R == 1 && sizeof(T) == 4) ? 32 / BY : 1) batch_step_kernel(const BatchDesc<T, C> *__restrict__ descs,
+__global__ void __launch_bounds__(32 * BY, sizeof(T) == 4 ? (R == 1 ? 32 / BY : R == 2 ? 24 / BY : 1) : 1) batch_step_kernel(const BatchDesc<T, C> *__restrict__ descs,
                                                             const int2 *__restrict__ work, int ntiles, int parity,
                                                             int groups)
 {

@@ -35,6 +35,38 @@ struct WallState {
     C rho, E;
 };
 
+// The two nodes next to side s at position pos along it: (x0, y0) on the
+// wall row or column, (x1, y1) one further in.
+template <typename T, typename C>
+__device__ __forceinline__ void wall_nodes(const StepArgs<T, C> &a, int s, int pos, int &x0, int &y0, int &x1,
+                                           int &y1)
+{
+    if (s == WEST) { x0 = 0; x1 = 1; y0 = y1 = pos; }
+    else if (s == EAST) { x0 = a.nx - 1; x1 = a.nx - 2; y0 = y1 = pos; }
+    else if (s == SOUTH) { y0 = 0; y1 = 1; x0 = x1 = pos; }
+    else { y0 = a.ny - 1; y1 = a.ny - 2; x0 = x1 = pos; }
+}
+
+// The outgoing normal links of side s: the unit link and the distance-2 link.
+__device__ __forceinline__ int out_unit(int s) { return s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2; }
+__device__ __forceinline__ int out_two(int s) { return s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10; }
+
+// Wall state of a temperature wall whose density makes the net normal mass
+// flux zero.  Every even moment of the wall equilibrium is proportional to
+// rho_w, so the anti-bounce-back links return 2 rho_w e_j; rho_w balances the
+// outgoing normal populations (the unit link from the first node, the
+// distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two), e the
+// even parts at unit density (zf_ea, zf_eb).  dout = deviation of those three
+// populations, summed first node unit, first node distance-2, second node
+// distance-2.
+template <typename C>
+__device__ __forceinline__ WallState<C> zero_flux_state(const WallArgs<C> &w, C dout)
+{
+    const C drho = (dout - w.zf_ea - C(2) * w.zf_eb) / (w.wsum + w.zf_ea + C(2) * w.zf_eb);
+    const C rho = C(1) + drho;
+    return {drho, drho * w.base + w.eT + C(13) * rho * (w.ux * w.ux + w.uy * w.uy)};
+}
+
 // Wall state at position `pos` along side `s`.  Out of line: only the nodes
 // next to a wall that needs data evaluate it; returned by value so that the
 // caller keeps it in registers (no stack frame).
@@ -43,30 +75,18 @@ __device__ __noinline__ WallState<C> wall_state(const StepArgs<T, C> &a, int s, 
 {
     const WallArgs<C> &w = a.wall[s];
     int x0, y0, x1, y1;
-    if (s == WEST) { x0 = 0; x1 = 1; y0 = y1 = pos; }
-    else if (s == EAST) { x0 = a.nx - 1; x1 = a.nx - 2; y0 = y1 = pos; }
-    else if (s == SOUTH) { y0 = 0; y1 = 1; x0 = x1 = pos; }
-    else { y0 = a.ny - 1; y1 = a.ny - 2; x0 = x1 = pos; }
+    wall_nodes(a, s, pos, x0, y0, x1, y1);
+    if (w.kind == WALL_MIXED && w.mass_flux) {
+        const int ja = out_unit(s), jb = out_two(s);
+        return zero_flux_state(w, ld(a, ja, x0, y0) + ld(a, jb, x0, y0) + ld(a, jb, x1, y1));
+    }
     C g0[Q], g1[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         g0[j] = ld(a, j, x0, y0);
         g1[j] = ld(a, j, x1, y1);
     }
-    C drho;
-    if (w.kind == WALL_MIXED && w.mass_flux) {
-        // every even moment of the wall equilibrium is proportional to rho_w,
-        // so the anti-bounce-back links return 2 rho_w e_j; rho_w balances the
-        // outgoing normal populations (unit link from the first node, the
-        // distance-2 link from both nodes): rho_w = out / (e_unit + 2 e_two),
-        // e the even parts at unit density (zf_ea, zf_eb)
-        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
-        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
-        const C dout = g0[ja] + g0[jb] + g1[jb];
-        drho = (dout - w.zf_ea - C(2) * w.zf_eb) / (w.wsum + w.zf_ea + C(2) * w.zf_eb);
-    } else {
-        drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
-    }
+    const C drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
     const C rho = C(1) + drho;
     C dE;
     if (w.kind == WALL_MIXED)
@@ -186,15 +206,32 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
     const int nx = a.nx, ny = a.ny;
     const bool yin = y0 >= 2 && y0 + R <= ny - 2;
     if (__all_sync(0xffffffffu, yin)) {
-        // lanes next to an x wall that needs data evaluate its state at their
-        // rows first (nothing else is live yet)
+        // Lanes next to an x wall that needs data need its state at their
+        // rows.  At a zero-flux temperature wall it takes three populations:
+        // their loads are issued here and summed after the pulls, so they
+        // share the pulls' round trip.  Other walls evaluate it out of line
+        // first (nothing else is live yet).
         const bool xedge = x < nx && (x < 2 || x >= nx - 2) && !a.per_x;
         const int side = x < 2 ? WEST : EAST;
+        const bool wdata = xedge && a.wall[side].needs_data;
+        const bool zf = a.wall[side].kind == WALL_MIXED && a.wall[side].mass_flux;
         WallState<C> st[R];
+        C zo[R][3];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             st[r] = {C(0), C(0)};
-            if (xedge && a.wall[side].needs_data) st[r] = wall_state(a, side, y0 + r);
+            zo[r][0] = zo[r][1] = zo[r][2] = C(0);
+            if (wdata) {
+                if (zf) {
+                    int x0, y0w, x1, y1w;
+                    wall_nodes(a, side, y0 + r, x0, y0w, x1, y1w);
+                    zo[r][0] = ld(a, out_unit(side), x0, y0w);
+                    zo[r][1] = ld(a, out_two(side), x0, y0w);
+                    zo[r][2] = ld(a, out_two(side), x1, y1w);
+                } else {
+                    st[r] = wall_state(a, side, y0 + r);
+                }
+            }
         }
         C f[R][Q];
         const T *base = a.fin + (long long)y0 * a.pitch;
@@ -210,6 +247,7 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
         if (x < 2 || x >= nx - 2) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
+                if (wdata && zf) st[r] = zero_flux_state(a.wall[side], zo[r][0] + zo[r][1] + zo[r][2]);
 #pragma unroll
                 for (int j = 0; j < Q; ++j) {
                     if (cvx(j) == 0) continue;
