@@ -135,13 +135,15 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
     const int sx_side = west ? WEST : EAST, sy_side = south ? SOUTH : NORTH;
     const int kind_x = a.wall[sx_side].kind, kind_y = a.wall[sy_side].kind;
     const bool nd_x = a.wall[sx_side].needs_data != 0, nd_y = a.wall[sy_side].needs_data != 0;
-    // the wall states at this node's position (a corner node's are the
-    // corner's: its x wall at its row, its y wall at its column), before the
-    // pulls so that they are not live across the calls
+    // the wall states at this node's position, before the pulls so that
+    // they are not live across the calls: a wall's own state where it needs
+    // data; at a corner node (the only one whose diagonal crosses both walls)
+    // both states enter the corner's correction when either wall needs data
     const bool near_x = !px && (x <= 1 || x >= nx - 2), near_y = !py && (y <= 1 || y >= ny - 2);
+    const bool corner_node = !px && !py && (x == 0 || x == nx - 1) && (y == 0 || y == ny - 1);
     WallState<C> stx = {C(0), C(0)}, sty = {C(0), C(0)};
-    if (near_x && (nd_x || nd_y)) stx = wall_state(a, sx_side, y);
-    if (near_y && (nd_x || nd_y)) sty = wall_state(a, sy_side, x);
+    if (near_x && (nd_x || (corner_node && nd_y))) stx = wall_state(a, sx_side, y);
+    if (near_y && (nd_y || (corner_node && nd_x))) sty = wall_state(a, sy_side, x);
     C v[Q];
     unsigned cross = 0u, neg = 0u, crx = 0u, cry = 0u;
 #pragma unroll
