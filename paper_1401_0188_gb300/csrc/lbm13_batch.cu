@@ -66,11 +66,46 @@ __global__ void __launch_bounds__(32 * BY, sizeof(T) == 4 ? (R == 1 ? 32 / BY : 
     }
 }
 
+// One block per tile (the grid the autotuner picks on uneven lattices): the
+// same per-node code without the run loop, the next-item prefetch and the
+// lattice comparison, so fewer registers stay live across the row groups.
+template <typename T, typename C, int R, int BY>
+__global__ void __launch_bounds__(32 * BY, sizeof(T) == 4 ? (R == 1 ? 32 / BY : R == 2 ? 24 / BY : 1) : 1) batch_tile_kernel(const BatchDesc<T, C> *__restrict__ descs,
+                                                            const int2 *__restrict__ work, int parity, int groups)
+{
+    __shared__ StepArgs<T, C> sa;
+    __shared__ int s_force;
+    __shared__ C slots[32 * BY][Q];
+    constexpr int kWords = int(sizeof(StepArgs<T, C>) / 16);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int2 w = __ldg(work + blockIdx.x);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
+        int4 *dst = reinterpret_cast<int4 *>(&sa);
+        for (int i = tid; i < kWords; i += 32 * BY) dst[i] = __ldg(src + i);
+        if (tid == 0) s_force = descs[w.x].force;
+    }
+    __syncthreads();
+    const int x = (w.y & 0xffff) * 32 + threadIdx.x;
+    const int yb = (w.y >> 16) * groups * (BY * R);
+    for (int g = 0; g < groups; ++g) {
+        const int y = yb + g * (BY * R);
+        if (y >= sa.ny) break;
+        if (s_force)
+            process_column<T, C, true, R>(sa, x, y + threadIdx.y * R, slots[tid]);
+        else
+            process_column<T, C, false, R>(sa, x, y + threadIdx.y * R, slots[tid]);
+    }
+}
+
 template <typename T, typename C, int R, int BY>
 cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int groups,
                             int grid, cudaStream_t s)
 {
-    batch_step_kernel<T, C, R, BY><<<grid, dim3(32, BY), 0, s>>>(descs, work, ntiles, parity, groups);
+    if (grid >= ntiles)
+        batch_tile_kernel<T, C, R, BY><<<ntiles, dim3(32, BY), 0, s>>>(descs, work, parity, groups);
+    else
+        batch_step_kernel<T, C, R, BY><<<grid, dim3(32, BY), 0, s>>>(descs, work, ntiles, parity, groups);
     return cudaGetLastError();
 }
 
