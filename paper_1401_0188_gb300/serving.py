@@ -75,11 +75,12 @@ def request_setup(req):
 
 
 def lattice_bytes(nx, ny, precision):
-    """Device bytes a request holds: two population buffers, wall corrections
-    and the FP64 reduction buffers."""
+    """Device bytes a request holds: two population buffers and the FP64
+    reduction buffers (six fields plus per-block partial sums, an upper
+    bound on the library's block count)."""
     elem = 8 if precision == lbm13.FP64 else 4
     pitch = (nx + 31) // 32 * 32
-    return 2 * 13 * elem * pitch * ny + elem * (16 * max(nx, ny) + 4) + 8 * (6 * nx * ny + 1216 * 16 + 32)
+    return 2 * 13 * elem * pitch * ny + 8 * (6 * nx * ny + 1216 * 16 + 32)
 
 
 def poisson_trace(n, rate, seed=5151, side_range=(64, 192), ra_range=(1e3, 1e5), Pr=0.71, tol=1e-7):
