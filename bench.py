@@ -174,8 +174,20 @@ def cpu_baseline(steps_target_s=12.0, n=512):
     t = time.perf_counter()
     lat.step(steps)
     dt = time.perf_counter() - t
+    # the same oracle on one thread, for a bounded few seconds
+    one = O.Lattice(n, n, p, nthreads=1)
+    one.set_equilibrium(1.0, ux, uy, (p["E0"] + 28) / 26)
+    t = time.perf_counter()
+    one.step(1)
+    per1 = time.perf_counter() - t
+    steps1 = max(1, int(0.33 * steps_target_s / max(per1, 1e-6)))
+    t = time.perf_counter()
+    one.step(steps1)
+    dt1 = time.perf_counter() - t
     return {"value": n * n * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n}x{n} periodic shear wave, {steps} steps, FP64 oracle, {cores} OpenMP threads"}
+            "sample": f"{n}x{n} periodic shear wave, {steps} steps, FP64 oracle, {cores} OpenMP threads",
+            "one_thread": {"value": n * n * steps1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                           "sample": f"{n}x{n}, {steps1} steps, 1 thread"}}
 
 
 def run_reference(args):
