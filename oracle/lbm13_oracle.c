@@ -58,6 +58,13 @@
  *   corners: a diagonal that crosses two walls at once bounces back with the
  *      mean of the two walls' data.
  *
+ * Parity unpinned: two sub-choices above pass every pin of the test suite
+ * when replaced by a plausible alternative (the mutation tests plant each
+ * alternative in a copy of this file): the half-force shift of R9 (equilibria
+ * at j instead of j + F/2 move only non-conserved moments by O(F)) and the
+ * corner mean (one wall's density instead changes one link of the four corner
+ * nodes).  Nothing the paper prints fixes either.
+ *
  * Storage: post-collision distributions f*(t), plane-major f[j][y][x], FP64.
  */
 #include <math.h>

@@ -42,7 +42,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # LBM13_ORACLE_LIB: an alternative build of lbm13_oracle.c (the
+        # mutation tests load copies with a planted mistake)
+        path = os.environ.get("LBM13_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         L.orc_create.restype = C.c_void_p

@@ -152,3 +152,24 @@ def test_parameter_set_is_linearly_stable(pstar, U):
     lat = O.Lattice(2, 2, pstar)
     J, _ = linear.collision_jacobian(lat, 1.0, U[0], U[1])
     assert linear.max_modulus(J, n=25) <= 1 + 1e-9
+
+
+def test_each_moment_relaxes_at_its_own_rate(pstar, rest):
+    """Sec. 2, the multiple-relaxation-time collision: a perturbation along one
+    non-conserved moment of the basis (the population vector whose moments are
+    that unit moment alone) leaves rho, E and j unchanged, so the equilibria do
+    not move, and one collision multiplies it by 1 - s_k.  The rates are those
+    of the parameter list (s_eps, s_varpi, s_r, s_XXe as given), s_q and s_XX
+    from 1/(sigma + 1/2) (sigma_XX from nu, R4; sigma_q the derived constant of
+    Eq. (d2q13-sigma-qx)), and R3 (each y partner takes its x moment's rate)."""
+    lat, J = rest
+    _, _, Minv = O.basis()
+    c = lat.constants()
+    s_q = 1.0 / (c["sigma_q"] + 0.5)
+    s_XX = 1.0 / (c["sigma_XX"] + 0.5)
+    assert c["sigma_XX"] == pytest.approx(104.0 * pstar["nu"] / c["A"], rel=1e-14)
+    rates = {2: pstar["s_eps"], 3: pstar["s_vpi"], 6: s_q, 7: s_q, 8: pstar["s_r"], 9: pstar["s_r"],
+             10: s_XX, 11: s_XX, 12: pstar["s_XXe"]}
+    for k, s in rates.items():
+        v = Minv[:, k]
+        assert np.allclose(J @ v, (1.0 - s) * v, rtol=0, atol=1e-8 * np.abs(v).max()), k
