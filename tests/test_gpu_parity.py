@@ -383,3 +383,37 @@ def test_allocator_failure_is_reported(L, pstar):
     assert out[14] == 10 and out[4] == pytest.approx(48 * 40, rel=1e-4)
     lib.lbm13_destroy(h)
     assert not live
+
+
+# ------------------------------------------------------- shape limits
+
+@pytest.mark.parametrize("nx,ny,walls", [(1 << 20, 4, "y"), (32, 32768, "x")])
+def test_limit_shapes_match_oracle(L, pstar, nx, ny, walls):
+    """The largest row (n_x = 2^20) and the tallest column (n_y = 32768) the
+    library accepts, each with walls across the short axis (temperature and
+    moving walls) and seeded random fields: FP64 parity with the oracle on every
+    node after 3 steps, alone and stepped through a one-lattice plan (its tile
+    coordinates reach column tile 32767 / row tile 8191)."""
+    T0 = _T0(pstar)
+    M, B = W.WALL_MIXED, W.WALL_BB
+    if walls == "y":
+        bnd = W.boundary(south=W.wall(M, 0.01, T0 + 0.002), north=W.wall(B, -0.02), wall_density=1)
+    else:
+        bnd = W.boundary(west=W.wall(M, -0.01, T0 - 0.002), east=W.wall(M, 0.0, T0 + 0.002))
+    t = W.random_fields(64, 64, T0, 77, du=0.01, drho=0.005, dT=0.003)
+    reps = (ny // 64 + 1, nx // 64 + 1)
+    fields = [np.ascontiguousarray(np.tile(a, reps)[:ny, :nx]) for a in t]
+    o, g = _pair(L, nx, ny, pstar, bnd)
+    _init_fields(o, g, fields)
+    o.step(3)
+    g.step(3)
+    mo, mg = o.macro(), g.macro()
+    assert max(_maxdiff(mo[i], mg[i]) for i in range(4)) <= 1e-12
+    h = L.Lattice(nx, ny, pstar, bnd)
+    h.set_state(*fields)
+    plan = L.Plan([h])
+    plan.set_config(1, 4, 0, 2, 1)
+    plan.step(3)
+    mh = h.macro()
+    assert max(_maxdiff(mo[i], mh[i]) for i in range(4)) <= 1e-12
+    plan.close()
