@@ -205,7 +205,7 @@ def main(argv=None):
     sub = ap.add_subparsers(dest="cmd", required=True)
     c = sub.add_parser("cavity")
     c.add_argument("--L", type=int, default=256)
-    c.add_argument("--Ra", type=float, nargs="+", default=[1e3, 1e4, 1e5])
+    c.add_argument("--Ra", type=float, nargs="+", default=[1e3, 1e4, 1e5, 1e6])
     c.add_argument("--Pr", type=float, default=0.71)
     c.add_argument("--tol", type=float, default=1e-8)
     c.add_argument("--check-every", type=int, default=1000)
