@@ -12,6 +12,7 @@
 
 #include "../../include/lbm13.h"
 #include "lbm13_internal.h"
+#include "lbm13_tma.h"
 
 using namespace lbm13;
 
@@ -971,6 +972,11 @@ struct lbm13_plan {
     std::vector<int> cur0;
     int parity = 0;  // parity of the next launch relative to cur0
     int R = 2, BY = 4, ctas = 8, order = 0, groups = 1, grid = 0, sms = 0, tried = 0;
+    // FP32: the lattices' tensor maps for the staged tiles (R = 4, BY = 4, one
+    // block per tile) and the word their bounded waits set when one runs out
+    void *maps = nullptr;
+    size_t maps_bytes = 0;
+    unsigned *tma_err = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     std::string err;
@@ -1014,6 +1020,76 @@ void plan_drop_graphs(lbm13_plan_t p)
         if (p->gexec[i]) { cudaGraphExecDestroy(p->gexec[i]); p->gexec[i] = nullptr; }
 }
 
+// cuTensorMapEncodeTiled, fetched through the runtime (no link against the
+// driver library); nullptr when the driver does not provide it.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled tensor_map_encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// The populations of one FP32 buffer as a tensor (x: nx, y: ny, plane: 13),
+// boxes of the staged tile, zeros outside the lattice.
+bool encode_lattice_map(lbm13_t h, const void *buf, CUtensorMap *m)
+{
+    const EncodeTiled fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(h->nx), cuuint64_t(h->ny), cuuint64_t(Q)};
+    const cuuint64_t strides[2] = {cuuint64_t(h->pitch) * 4u, cuuint64_t(h->plane) * 4u};
+    const cuuint32_t box[3] = {cuuint32_t(kTmaX), cuuint32_t(kTmaY), cuuint32_t(Q)};
+    const cuuint32_t step[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(buf), dims, strides, box, step,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of every lattice of an FP32 plan for both parities (lattices
+// narrower than 64 columns or lower than the box keep global loads).
+int plan_upload_maps(lbm13_plan_t p)
+{
+    std::vector<LatticeMaps> host(p->lats.size());
+    for (size_t i = 0; i < p->lats.size(); ++i) {
+        lbm13_t h = p->lats[i];
+        std::memset(&host[i], 0, sizeof(LatticeMaps));
+        const int cur = p->cur0[i];
+        host[i].use = h->nx >= 64 && h->ny >= kTmaY && encode_lattice_map(h, h->buf[cur], &host[i].map[0]) &&
+                      encode_lattice_map(h, h->buf[cur ^ 1], &host[i].map[1]);
+    }
+    const size_t bytes = host.size() * sizeof(LatticeMaps);
+    if (!p->maps || p->maps_bytes < bytes) {
+        plan_free(p, p->maps);
+        p->maps = plan_alloc(p, bytes);
+        p->maps_bytes = bytes;
+        if (!p->maps) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan's tensor maps");
+    }
+    if (!p->tma_err) {
+        p->tma_err = static_cast<unsigned *>(plan_alloc(p, sizeof(unsigned)));
+        if (!p->tma_err) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan's error word");
+        cudaError_t e = cudaMemsetAsync(p->tma_err, 0, sizeof(unsigned), p->stream);
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan error word: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMemcpyAsync(p->maps, host.data(), bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("tensor map upload: ") + cudaGetErrorString(e));
+    return LBM13_OK;
+}
+
 template <typename T, typename C>
 int plan_upload_descs(lbm13_plan_t p)
 {
@@ -1037,6 +1113,10 @@ int plan_upload_descs(lbm13_plan_t p)
     cudaError_t e = cudaMemcpyAsync(p->desc, host.data(), bytes, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
+    if (sizeof(T) == 4) {
+        const int rc = plan_upload_maps(p);
+        if (rc != LBM13_OK) return rc;
+    }
     p->parity = 0;
     plan_drop_graphs(p);
     return LBM13_OK;
@@ -1091,6 +1171,10 @@ int plan_build_work(lbm13_plan_t p)
 
 cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
 {
+    if (p->precision != LBM13_FP64 && p->R == 4 && p->BY == 4 && p->grid >= p->ntiles && p->maps && p->tma_err)
+        return launch_batch_tma(static_cast<const BatchDesc<float, float> *>(p->desc),
+                                static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
+                                p->ntiles, parity, p->groups, p->tma_err, s);
     if (p->precision == LBM13_FP64) {
         const auto *d = static_cast<const BatchDesc<double, double> *>(p->desc);
         return launch_batch<double, double>(d, static_cast<const int2 *>(p->work), p->ntiles, parity, p->R, p->BY,
@@ -1206,6 +1290,8 @@ void lbm13_plan_destroy(lbm13_plan_t p)
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     plan_free(p, p->desc);
     plan_free(p, p->work);
+    plan_free(p, p->maps);
+    plan_free(p, p->tma_err);
     plan_free(p, p->res_dev);
     delete p;
 }
@@ -1270,6 +1356,13 @@ int lbm13_plan_residual(lbm13_plan_t p, double *out)
     cudaError_t e = cudaMemcpyAsync(out, p->res_dev, bytes, cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan residual download: ") + cudaGetErrorString(e));
+    if (p->tma_err) {
+        unsigned word = 0;
+        e = cudaMemcpy(&word, p->tma_err, sizeof word, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && word) e = cudaMemset(p->tma_err, 0, sizeof word);
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan error word: ") + cudaGetErrorString(e));
+        if (word) return pfail(p, LBM13_ETIMEOUT, "a staged tile's tensor copy did not complete within 1 s");
+    }
     bool bad = false;
     for (size_t i = 0; i < p->lats.size(); ++i) {
         p->lats[i]->have_snap = 1;

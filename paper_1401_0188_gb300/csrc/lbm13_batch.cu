@@ -4,6 +4,7 @@
 // The per-node device code is the one-lattice kernel's (lbm13_stepdev.cuh), so
 // a lattice gives bit-identical results alone or in a plan.
 #include "lbm13_internal.h"
+#include "lbm13_tma.h"
 
 // Each launch reads only what earlier launches wrote: the read-only path.
 #define LBM13_LDG(p) __ldg(p)
@@ -98,6 +99,184 @@ __global__ void __launch_bounds__(32 * BY, sizeof(T) == 4 ? (R == 1 ? 32 / BY : 
     }
 }
 
+// ------------------------------------------------ tensor-map staged tiles
+//
+// FP32 only.  Each block takes one tile of 32 columns x 16 `groups` rows in
+// slabs of 8; one elected thread loads each slab (with its halo, all 13
+// planes) by one tensor copy into shared memory, completion signalled on an
+// mbarrier, the next slab issued once every warp is done with the current
+// one.  A warp takes rows w and w + 4 of the slab and pulls its 13
+// populations from shared memory; the lanes at an x edge replace
+// the links that cross it with process_column's rules (global loads), and the
+// rows within two of a y edge go through process_column itself, so the results
+// are bit-identical to the other kernels.
+
+__device__ __forceinline__ unsigned long long tma_clock()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_slab(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(0), "r"(bar)
+        : "memory");
+}
+
+// Wait for phase `phase` of the barrier to complete, for at most 1 s.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase)
+{
+    const unsigned long long end = tma_clock() + 1000000000ull;
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (tma_clock() > end) return false;
+    }
+}
+
+// Row r of the slab in `tile` (its row 0 is the slab's first row minus 2,
+// its column 0 is x0 - 4): node (x, y) of a row at least two from the bottom
+// and top edges.
+template <bool Force>
+__device__ __forceinline__ void tma_row(const StepArgs<float, float> &a, const float *tile, int r, int x, int y)
+{
+    const int nx = a.nx;
+    const bool xedge = x < nx && (x < 2 || x >= nx - 2) && !a.per_x;
+    const int side = x < 2 ? WEST : EAST;
+    WallState<float> st = {0.0f, 0.0f};
+    if (xedge && a.wall[side].needs_data) {
+        const WallArgs<float> &w = a.wall[side];
+        if (w.kind == WALL_MIXED && w.mass_flux) {
+            int x0, y0w, x1, y1w;
+            wall_nodes(a, side, y, x0, y0w, x1, y1w);
+            st = zero_flux_state(w, ld(a, out_unit(side), x0, y0w) + ld(a, out_two(side), x0, y0w) +
+                                        ld(a, out_two(side), x1, y1w));
+        } else {
+            st = wall_state(a, side, y);
+        }
+    }
+    float f[Q];
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) f[j] = tile[(j * kTmaY + r + 2 - cvy(j)) * kTmaX + lane + 4 - cvx(j)];
+    if (x >= nx) return;
+    if (x < 2 || x >= nx - 2) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            if (cvx(j) == 0) continue;
+            const int sx = x - cvx(j);
+            if (sx >= 0 && sx < nx) continue;
+            if (a.per_x)
+                f[j] = ld(a, j, sx < 0 ? sx + nx : sx - nx, y - cvy(j));
+            else
+                f[j] = cross_wall(a, side, j, x, y, st);
+        }
+    }
+    collide<Force>(f, a.k);
+    store(a, x, y, f);
+}
+
+template <bool Force>
+__device__ __forceinline__ void tma_slabs(const StepArgs<float, float> &a, const CUtensorMap *map, float *stage,
+                                          unsigned bar0, int x0, int yb, int nslab, int tid, float *slot,
+                                          unsigned *err)
+{
+    const int x = x0 + threadIdx.x, ny = a.ny;
+    const unsigned st0 = static_cast<unsigned>(__cvta_generic_to_shared(stage));
+    if (tid == 0) tma_slab(st0, map, x0 - 4, yb - 2, bar0);
+    for (int g = 0; g < nslab; ++g) {
+        const bool ok = mbar_wait(bar0, g & 1);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not complete in time: report, wait (bounded) once
+            // more so that it does not land after the block, leave
+            if (tid == 0) atomicOr(err, 1u);
+            mbar_wait(bar0, g & 1);
+            return;
+        }
+        const float *tile = stage;
+#pragma unroll 1
+        for (int i = 0; i < kTmaRows / 4; ++i) {
+            const int r = threadIdx.y + 4 * i;
+            const int y = yb + g * kTmaRows + r;
+            if (y >= ny) break;
+            if (__all_sync(0xffffffffu, y >= 2 && y + 1 <= ny - 2))
+                tma_row<Force>(a, tile, r, x, y);
+            else
+                process_column<float, float, Force, 1>(a, x, y, slot);
+        }
+        __syncthreads();
+        if (tid == 0 && g + 1 < nslab) tma_slab(st0, map, x0 - 4, yb + (g + 1) * kTmaRows - 2, bar0);
+    }
+}
+
+__global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float, float> *__restrict__ descs,
+                                                           const LatticeMaps *__restrict__ maps,
+                                                           const int2 *__restrict__ work, int parity, int groups,
+                                                           unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    __shared__ StepArgs<float, float> sa;
+    __shared__ float slots[128][Q];
+    __shared__ __align__(8) unsigned long long bars[1];
+    __shared__ int s_force, s_use;
+    constexpr int kWords = int(sizeof(StepArgs<float, float>) / 16);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int2 w = __ldg(work + blockIdx.x);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
+        int4 *dst = reinterpret_cast<int4 *>(&sa);
+        for (int i = tid; i < kWords; i += 128) dst[i] = __ldg(src + i);
+    }
+    const unsigned bar0 = static_cast<unsigned>(__cvta_generic_to_shared(&bars[0]));
+    if (tid == 0) {
+        s_force = descs[w.x].force;
+        s_use = maps[w.x].use;
+        mbar_init(bar0);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int x0 = (w.y & 0xffff) * 32;
+    const int yb = (w.y >> 16) * groups * 16;
+    const int ny = sa.ny;
+    const int nslab = min(groups * (16 / kTmaRows), (ny - yb + kTmaRows - 1) / kTmaRows);
+    float *stage = reinterpret_cast<float *>(tma_smem);
+    if (s_use) {
+        const CUtensorMap *map = &maps[w.x].map[parity];
+        if (s_force)
+            tma_slabs<true>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err);
+        else
+            tma_slabs<false>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err);
+        return;
+    }
+    // a lattice without tensor maps: one row per thread through global loads
+    const int x = x0 + threadIdx.x;
+    for (int g = 0; g < nslab; ++g) {
+        for (int i = 0; i < kTmaRows / 4; ++i) {
+            const int y = yb + g * kTmaRows + threadIdx.y + 4 * i;
+            if (y >= ny) break;
+            if (s_force)
+                process_column<float, float, true, 1>(sa, x, y, slots[tid]);
+            else
+                process_column<float, float, false, 1>(sa, x, y, slots[tid]);
+        }
+    }
+}
+
 template <typename T, typename C, int R, int BY>
 cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int groups,
                             int grid, cudaStream_t s)
@@ -129,6 +308,22 @@ cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int nti
     if (R == 2 && BY == 2) return launch_batch_rb<T, C, 2, 2>(descs, work, ntiles, parity, groups, grid, s);
     if (R == 1 && BY == 8) return launch_batch_rb<T, C, 1, 8>(descs, work, ntiles, parity, groups, grid, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
+                             int ntiles, int parity, int groups, unsigned *err, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (groups < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    batch_tma_kernel<<<ntiles, dim3(32, 4), kTmaSmem, s>>>(descs, maps, work, parity, groups, err);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_batch<double, double>(const BatchDesc<double, double> *, const int2 *, int, int, int, int,
