@@ -340,7 +340,9 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
 /* Choose a configuration: (R, BY) in {(1,4), (2,4), (4,4), (2,2), (1,8)},
  * ctas_per_sm 0 (one CTA per tile) .. 64, order 0 by lattice, 1 round robin,
  * 2 largest first, groups 1 .. 64 row groups of BY * R rows per tile (a tile
- * is 32 columns x groups * BY * R rows).  LBM13_EINVAL outside these. */
+ * is 32 columns x groups * BY * R rows).  LBM13_EINVAL outside these.  In an
+ * FP32 plan, (4,4) with one CTA per tile stages each tile's populations
+ * through shared memory by tensor copies (TMA), 8 rows at a time. */
 int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
 /* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried
@@ -352,7 +354,9 @@ int lbm13_plan_config(lbm13_plan_t p, int64_t out[9]);
  * synchronisation of the plan's stream.  Each lattice's residual snapshot
  * advances as with lbm13_residual (a lattice's first call allocates its
  * reduction buffers through its own allocator).  Returns LBM13_EDIVERGED,
- * after filling out, when a lattice holds non-finite populations. */
+ * after filling out, when a lattice holds non-finite populations, and
+ * LBM13_ETIMEOUT when a staged tile's tensor copy did not complete within
+ * 1 s since the last call (its tile was left unstepped). */
 int lbm13_plan_residual(lbm13_plan_t p, double *out);
 
 /* Largest lattice (nx * ny) that lbm13_totals_noalloc accepts. */
