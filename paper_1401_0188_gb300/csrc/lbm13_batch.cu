@@ -3,6 +3,8 @@
 // (lattice, tile) pairs, each lattice's arguments read from a descriptor array.
 // The per-node device code is the one-lattice kernel's (lbm13_stepdev.cuh), so
 // a lattice gives bit-identical results alone or in a plan.
+#include <atomic>
+
 #include "lbm13_internal.h"
 #include "lbm13_tma.h"
 
@@ -315,12 +317,17 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
 {
     if (ntiles <= 0) return cudaSuccess;
     if (groups < 1) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
+    // the kernel's shared-memory allowance is a per-device attribute: raise
+    // it once on each device that launches it
+    static std::atomic<unsigned long long> raised{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(raised.load() & bit)) {
+        e = cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        raised.fetch_or(bit);
     }
     batch_tma_kernel<<<ntiles, dim3(32, 4), kTmaSmem, s>>>(descs, maps, work, parity, groups, err);
     return cudaGetLastError();
