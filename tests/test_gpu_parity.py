@@ -417,3 +417,31 @@ def test_limit_shapes_match_oracle(L, pstar, nx, ny, walls):
     mh = h.macro()
     assert max(_maxdiff(mo[i], mh[i]) for i in range(4)) <= 1e-12
     plan.close()
+
+
+def test_staggered_invariant_at_size(L, pstar):
+    """Sec. 2 stencil: S = sum of (-1)^(x+y) (15 rho + E) is conserved exactly
+    by the step on a periodic lattice (the unit links, the only ones that change
+    the parity of x + y, carry no 15 rho + E).  A 2048 x 2048 FP64 lattice from
+    a seeded random state keeps S to round-off over 300 steps, while the
+    staggered sum of rho alone moves."""
+    n = 2048
+    g = L.Lattice(n, n, pstar, precision=0)
+    T0 = _T0(pstar)
+    t = W.random_fields(64, 64, T0, 9, du=0.01, drho=0.005, dT=0.003)
+    rho, ux, uy, T = [np.ascontiguousarray(np.tile(a, (n // 64, n // 64))) for a in t]
+    rng = np.random.Generator(np.random.PCG64(31))
+    rho = rho * (1.0 + 1e-3 * rng.standard_normal((n, n)))
+    g.set_state(rho, ux, uy, T)
+    sign = (-1.0) ** np.add.outer(np.arange(n), np.arange(n))
+
+    def staggered():
+        m = g.moments(1 | 2)  # planes rho, E
+        return float(np.sum(sign * (15.0 * m[0] + m[1]))), float(np.sum(sign * m[0])), float(np.abs(m[0]).sum())
+
+    s0, r0, scale = staggered()
+    g.step(300)
+    s1, r1, _ = staggered()
+    assert abs(s0) > 1e-3
+    assert abs(s1 - s0) <= 1e-13 * 15.0 * scale
+    assert abs(r1 - r0) > 1e3 * abs(s1 - s0)
