@@ -205,6 +205,13 @@ void lbm13_destroy(lbm13_t h);
 /* Last error message of this handle (static storage per handle). */
 const char *lbm13_last_error(lbm13_t h);
 
+/* Debug builds (compiled with LBM13_DEBUG): *count = the number of population
+ * loads and stores of the step kernels on this lattice so far that fell
+ * outside it (plane >= 13, row >= ny or column >= nx); each was counted and
+ * redirected to the buffer's first element instead of being performed.
+ * Release builds return LBM13_EINVAL with *count = 0 (nothing is checked). */
+int lbm13_debug_violations(lbm13_t h, unsigned long long *count);
+
 /* Change the stream the following calls are ordered on. */
 int lbm13_set_stream(lbm13_t h, void *stream);
 

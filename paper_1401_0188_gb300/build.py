@@ -12,6 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm13.so")
+# bounds-checked build (LBM13_DEBUG): every population access of the step
+# kernels is checked and counted (lbm13_debug_violations)
+DEBUG_OUT = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_OUT, "liblbm13_debug.so")
 SOURCES = ["lbm13_step.cu", "lbm13_batch.cu", "lbm13_multi.cu", "lbm13_aux.cu", "lbm13_api.cu", "lbm13_noalloc.cu", "lbm13_linear.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -29,15 +33,18 @@ def _deps():
     return files
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(OUT, exist_ok=True)
+def build(force=False, verbose=False, extra=(), debug=False):
+    out, lib = (DEBUG_OUT, DEBUG_LIB) if debug else (OUT, LIB)
+    if debug:
+        extra = (*extra, "-DLBM13_DEBUG")
+    os.makedirs(out, exist_ok=True)
     newest = max(os.path.getmtime(f) for f in _deps())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest and (debug or not extra):
+        return lib
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        obj = os.path.join(out, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -51,11 +58,11 @@ def build(force=False, verbose=False, extra=()):
     if verbose:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -26,6 +26,7 @@ struct lbm13_lattice {
     bool has_alloc = false;
     cudaStream_t stream = nullptr;
     void *buf[2] = {nullptr, nullptr};
+    unsigned long long *bad = nullptr;  // debug builds: accesses outside the lattice
     int cur = 0;
     long long t = 0;
     double derived[LBM13_DERIVED_COUNT] = {};
@@ -368,6 +369,9 @@ StepArgs<T, C> step_args(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C>
     a.pitch = h->pitch;
     a.plane = h->plane;
     a.k = k;
+#ifdef LBM13_DEBUG
+    a.bad = h->bad;
+#endif
     for (int s = 0; s < 4; ++s) a.wall[s] = w[s];
     for (int c = 0; c < 4; ++c)
         for (int m = 0; m < 5; ++m) a.corner_poly[c][m] = C(h->corner_poly[c][m]);
@@ -560,6 +564,21 @@ int lbm13_linear_growth(const lbm13_params *params, double ux, double uy, int n,
 
 const char *lbm13_last_error(lbm13_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
+int lbm13_debug_violations(lbm13_t h, unsigned long long *count)
+{
+    if (!h || !count) return fail(h, LBM13_EINVAL, "NULL argument");
+#ifdef LBM13_DEBUG
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaMemcpyAsync(count, h->bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "debug access counter");
+    return LBM13_OK;
+#else
+    *count = 0;
+    return fail(h, LBM13_EINVAL, "built without LBM13_DEBUG: population accesses are not checked");
+#endif
+}
+
 int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary, int precision,
                  const lbm13_allocator *alloc, void *stream, lbm13_t *out)
 {
@@ -626,6 +645,13 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
             return fail(nullptr, LBM13_ENOMEM, "allocator returned NULL for the population buffers");
         }
     }
+#ifdef LBM13_DEBUG
+    h->bad = static_cast<unsigned long long *>(dev_alloc(h, sizeof(unsigned long long)));
+    if (!h->bad || cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), h->stream) != cudaSuccess) {
+        lbm13_destroy(h);
+        return fail(nullptr, LBM13_ENOMEM, "debug access counter");
+    }
+#endif
     // deviation 0 everywhere = the rest state rho = 1, u = 0, T = T0
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = cudaMemsetAsync(h->buf[i], 0, h->state_bytes, h->stream);
@@ -647,6 +673,7 @@ void lbm13_destroy(lbm13_t h)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (int i = 0; i < 2; ++i) dev_free(h, h->buf[i], h->state_bytes);
+    if (h->bad) dev_free(h, h->bad, sizeof(unsigned long long));
     if (h->red_mem) {
         const long long n = (long long)h->nx * h->ny;
         dev_free(h, h->red_mem, (size_t(6 * n) + size_t(h->rb.nblocks) * kPartials + 32) * sizeof(double));

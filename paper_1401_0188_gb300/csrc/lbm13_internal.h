@@ -66,6 +66,9 @@ struct alignas(16) StepArgs {
     long long plane;  // elements per population plane (ny * pitch)
     Coef<C> k;
     WallArgs<C> wall[4];
+#ifdef LBM13_DEBUG
+    unsigned long long *bad;  // debug builds: population accesses found outside the lattice
+#endif
 };
 
 // One lattice of a batched launch: its arguments for both buffer parities

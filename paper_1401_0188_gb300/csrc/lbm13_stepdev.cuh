@@ -20,10 +20,33 @@ namespace lbm13 {
 
 namespace {
 
+// Debug builds (LBM13_DEBUG) check every population access against the
+// lattice (plane below 13, row below ny, column below nx): an access outside
+// it is counted in *a.bad and redirected to the buffer's first element, so it
+// neither faults nor corrupts; release builds pass the pointer through.
+template <typename T, typename C, typename P>
+__device__ __forceinline__ P *chk(const StepArgs<T, C> &a, P *base, P *p)
+{
+#ifdef LBM13_DEBUG
+    const long long i = p - base;
+    bool out = i < 0;
+    if (!out) {
+        const long long j = i / a.plane, rem = i - j * a.plane;
+        const long long y = rem / a.pitch, x = rem - y * a.pitch;
+        out = j >= Q || y >= a.ny || x >= a.nx;
+    }
+    if (out) {
+        atomicAdd(a.bad, 1ull);
+        return base;
+    }
+#endif
+    return p;
+}
+
 template <typename T, typename C>
 __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
 {
-    return C(LBM13_LDG(a.fin + (long long)j * a.plane + (long long)y * a.pitch + x));
+    return C(LBM13_LDG(chk(a, a.fin, a.fin + (long long)j * a.plane + (long long)y * a.pitch + x)));
 }
 
 // ------------------------------------------------------ boundary links
@@ -160,7 +183,7 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
         const int js = c ? copp(j) : j;
         const bool n = (ox && !oy && cvy(j) == 0 && kind_x == WALL_MIXED) ||
                        (oy && !ox && cvx(j) == 0 && kind_y == WALL_MIXED);
-        v[j] = C(LBM13_LDG(a.fin + (long long)js * a.plane + (long long)ys * a.pitch + xs));
+        v[j] = C(LBM13_LDG(chk(a, a.fin, a.fin + (long long)js * a.plane + (long long)ys * a.pitch + xs)));
         cross |= (c ? 1u : 0u) << j;
         neg |= (n ? 1u : 0u) << j;
         crx |= (ox ? 1u : 0u) << j;
@@ -190,7 +213,7 @@ __device__ __forceinline__ void store(const StepArgs<T, C> &a, int x, int y, con
 {
     T *p = a.fout + (long long)y * a.pitch + x;
 #pragma unroll
-    for (int j = 0; j < Q; ++j) p[(long long)j * a.plane] = T(f[j]);
+    for (int j = 0; j < Q; ++j) *chk(a, a.fout, p + (long long)j * a.plane) = T(f[j]);
 }
 
 // ------------------------------------------------------------- the step
@@ -242,7 +265,7 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
 #pragma unroll
             for (int j = 0; j < Q; ++j) {
                 const int xs = min(max(x - cvx(j), 0), nx - 1);
-                f[r][j] = C(LBM13_LDG(base + (long long)j * a.plane + (long long)(r - cvy(j)) * a.pitch + xs));
+                f[r][j] = C(LBM13_LDG(chk(a, a.fin, base + (long long)j * a.plane + (long long)(r - cvy(j)) * a.pitch + xs)));
             }
         }
         if (x >= nx) return;

@@ -37,7 +37,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
-           "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth")
+           "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations")
 
 
 class Lbm13Error(RuntimeError):
@@ -72,7 +72,9 @@ _lib = None
 
 
 def library_path():
-    return _build.LIB
+    """The release library, or the bounds-checked one (built with
+    build.build(debug=True)) when LBM13_DEBUG_BUILD=1."""
+    return _build.DEBUG_LIB if os.environ.get("LBM13_DEBUG_BUILD") == "1" else _build.LIB
 
 
 def lib():
@@ -110,6 +112,7 @@ def lib():
         "lbm13_set_persistent": (C.c_int, [vp, C.c_int]),
         "lbm13_linear_growth": (C.c_int, [C.POINTER(Params), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]),
         "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
+        "lbm13_debug_violations": (C.c_int, [vp, C.POINTER(C.c_ulonglong)]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
@@ -353,6 +356,13 @@ class Lattice:
             return out
         _check(st, self._h)
         return out
+
+    def debug_violations(self):
+        """Out-of-lattice population accesses counted by a bounds-checked
+        build (raises on a release build, which checks nothing)."""
+        n = C.c_ulonglong(0)
+        _check(lib().lbm13_debug_violations(self._h, C.byref(n)), self._h)
+        return int(n.value)
 
     def set_persistent(self, mode):
         """PERSISTENT_AUTO (default), PERSISTENT_OFF or PERSISTENT_ON: whether
