@@ -352,6 +352,14 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
  * through shared memory by tensor copies (TMA), 8 rows at a time. */
 int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
+/* Self-check of the staged tiles' bounded wait (FP32 plan set to R = 4,
+ * BY = 4, one CTA per tile, else LBM13_EINVAL): one staged launch with every
+ * wait limited to timeout_s (1e-3 .. 2 s) and, when withhold != 0, no tensor
+ * copy issued, so that every wait runs out and each block reports and leaves
+ * without writing.  *timed_out = 1 when the error word was set (it is cleared
+ * again).  The plan does not advance: the lattices keep their states. */
+int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *timed_out);
+
 /* out: R, BY, ctas_per_sm, order, tiles, grid, total nodes, candidates tried
  * by the last tune, groups. */
 int lbm13_plan_config(lbm13_plan_t p, int64_t out[9]);

@@ -1340,6 +1340,28 @@ int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int or
     return plan_build_work(p);
 }
 
+int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *timed_out)
+{
+    if (!p || !timed_out || !(timeout_s >= 1e-3 && timeout_s <= 2.0))
+        return pfail(p, LBM13_EINVAL, "NULL argument or timeout_s outside [1e-3, 2]");
+    if (p->precision == LBM13_FP64 || p->R != 4 || p->BY != 4 || p->grid < p->ntiles || !p->maps || !p->tma_err)
+        return pfail(p, LBM13_EINVAL, "the plan is not on the staged FP32 tiles (R = 4, BY = 4, one CTA per tile)");
+    DeviceGuard g(p->device);
+    int rc = plan_sync_parity(p);
+    if (rc != LBM13_OK) return rc;
+    unsigned word = 0;
+    cudaError_t e = launch_batch_tma(static_cast<const BatchDesc<float, float> *>(p->desc),
+                                     static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
+                                     p->ntiles, p->parity, p->groups, p->tma_err, p->stream, withhold ? 0 : 1,
+                                     (unsigned long long)(timeout_s * 1e9));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&word, p->tma_err, sizeof word, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->tma_err, 0, sizeof word);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("staged tile check: ") + cudaGetErrorString(e));
+    *timed_out = word != 0u;
+    return LBM13_OK;
+}
+
 int lbm13_plan_config(lbm13_plan_t p, int64_t out[9])
 {
     if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");

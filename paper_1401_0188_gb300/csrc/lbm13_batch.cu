@@ -134,10 +134,10 @@ __device__ __forceinline__ void tma_slab(unsigned dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Wait for phase `phase` of the barrier to complete, for at most 1 s.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase)
+// Wait for phase `phase` of the barrier to complete, for at most wait_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, unsigned long long wait_ns)
 {
-    const unsigned long long end = tma_clock() + 1000000000ull;
+    const unsigned long long end = tma_clock() + wait_ns;
     for (;;) {
         unsigned done;
         asm volatile(
@@ -195,18 +195,18 @@ __device__ __forceinline__ void tma_row(const StepArgs<float, float> &a, const f
 template <bool Force>
 __device__ __forceinline__ void tma_slabs(const StepArgs<float, float> &a, const CUtensorMap *map, float *stage,
                                           unsigned bar0, int x0, int yb, int nslab, int tid, float *slot,
-                                          unsigned *err)
+                                          unsigned *err, int issue, unsigned long long wait_ns)
 {
     const int x = x0 + threadIdx.x, ny = a.ny;
     const unsigned st0 = static_cast<unsigned>(__cvta_generic_to_shared(stage));
-    if (tid == 0) tma_slab(st0, map, x0 - 4, yb - 2, bar0);
+    if (tid == 0 && issue) tma_slab(st0, map, x0 - 4, yb - 2, bar0);
     for (int g = 0; g < nslab; ++g) {
-        const bool ok = mbar_wait(bar0, g & 1);
+        const bool ok = mbar_wait(bar0, g & 1, wait_ns);
         if (__syncthreads_or(!ok)) {
             // the copy did not complete in time: report, wait (bounded) once
             // more so that it does not land after the block, leave
             if (tid == 0) atomicOr(err, 1u);
-            mbar_wait(bar0, g & 1);
+            if (issue) mbar_wait(bar0, g & 1, wait_ns);
             return;
         }
         const float *tile = stage;
@@ -221,14 +221,14 @@ __device__ __forceinline__ void tma_slabs(const StepArgs<float, float> &a, const
                 process_column<float, float, Force, 1>(a, x, y, slot);
         }
         __syncthreads();
-        if (tid == 0 && g + 1 < nslab) tma_slab(st0, map, x0 - 4, yb + (g + 1) * kTmaRows - 2, bar0);
+        if (tid == 0 && issue && g + 1 < nslab) tma_slab(st0, map, x0 - 4, yb + (g + 1) * kTmaRows - 2, bar0);
     }
 }
 
 __global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float, float> *__restrict__ descs,
                                                            const LatticeMaps *__restrict__ maps,
                                                            const int2 *__restrict__ work, int parity, int groups,
-                                                           unsigned *err)
+                                                           unsigned *err, int issue, unsigned long long wait_ns)
 {
     extern __shared__ __align__(128) unsigned char tma_smem[];
     __shared__ StepArgs<float, float> sa;
@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float
     if (s_use) {
         const CUtensorMap *map = &maps[w.x].map[parity];
         if (s_force)
-            tma_slabs<true>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err);
+            tma_slabs<true>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err, issue, wait_ns);
         else
-            tma_slabs<false>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err);
+            tma_slabs<false>(sa, map, stage, bar0, x0, yb, nslab, tid, slots[tid], err, issue, wait_ns);
         return;
     }
     // a lattice without tensor maps: one row per thread through global loads
@@ -313,7 +313,8 @@ cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int nti
 }
 
 cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
-                             int ntiles, int parity, int groups, unsigned *err, cudaStream_t s)
+                             int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue,
+                             unsigned long long wait_ns)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (groups < 1) return cudaErrorInvalidValue;
@@ -329,7 +330,7 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
         if (e != cudaSuccess) return e;
         raised.fetch_or(bit);
     }
-    batch_tma_kernel<<<ntiles, dim3(32, 4), kTmaSmem, s>>>(descs, maps, work, parity, groups, err);
+    batch_tma_kernel<<<ntiles, dim3(32, 4), kTmaSmem, s>>>(descs, maps, work, parity, groups, err, issue, wait_ns);
     return cudaGetLastError();
 }
 

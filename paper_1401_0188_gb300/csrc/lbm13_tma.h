@@ -31,10 +31,13 @@ struct LatticeMaps {
 };
 
 // Staged batched step: one block per tile of 32 columns x 16 groups rows (two
-// slabs per row group of the R = 4, BY = 4 tile shape); the
-// wait for each slab is bounded (1 s by the global timer), after which the
-// block sets *err, waits (bounded) for its copy in flight and returns.
+// slabs per row group of the R = 4, BY = 4 tile shape); the wait for each
+// slab is bounded (wait_ns by the global timer, 1 s in a step), after which
+// the block sets *err, waits (bounded) for its copy in flight and returns.
+// issue = 0 withholds the copies, so that every wait runs out (the self-check
+// of the bounded wait; nothing is written then).
 cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
-                             int ntiles, int parity, int groups, unsigned *err, cudaStream_t s);
+                             int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue = 1,
+                             unsigned long long wait_ns = 1000000000ull);
 
 }  // namespace lbm13

@@ -37,7 +37,8 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_residual", "lbm13_time", "lbm13_synchronize", "lbm13_plan_create", "lbm13_plan_destroy",
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
-           "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations")
+           "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
+           "lbm13_plan_tma_check")
 
 
 class Lbm13Error(RuntimeError):
@@ -113,6 +114,7 @@ def lib():
         "lbm13_linear_growth": (C.c_int, [C.POINTER(Params), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]),
         "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
         "lbm13_debug_violations": (C.c_int, [vp, C.POINTER(C.c_ulonglong)]),
+        "lbm13_plan_tma_check": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
@@ -443,6 +445,13 @@ class Plan:
             return out
         _pcheck(st, self._h)
         return out
+
+    def tma_check(self, timeout_s, withhold=True):
+        """Self-check of the staged tiles' bounded wait: True when the waits
+        ran out (expected exactly when the copies are withheld)."""
+        out = C.c_int(0)
+        _pcheck(lib().lbm13_plan_tma_check(self._h, float(timeout_s), 1 if withhold else 0, C.byref(out)), self._h)
+        return bool(out.value)
 
     def config(self):
         out = (C.c_int64 * 9)()

@@ -87,6 +87,25 @@ def test_every_configuration_is_bit_identical(L, precision):
     plan.close()
 
 
+def test_staged_tile_wait_is_bounded(L):
+    """The staged (tensor-copy) tiles wait on an mbarrier with a time limit:
+    with the copies withheld every wait runs out, the error word is set and
+    read back, and nothing is written; with the copies issued no wait runs
+    out; the plan then steps on, bit-identical to lattices stepped alone."""
+    a, b = _twins(L, 1)
+    plan = L.Plan(a)
+    plan.set_config(4, 4, 0, 2, 1)
+    before = [g.save() for g in a]
+    assert plan.tma_check(0.02, withhold=True) is True
+    assert [g.save() for g in a] == before
+    assert plan.tma_check(0.5, withhold=False) is False
+    plan.step(5)
+    for g in b:
+        g.step(5)
+    _same(a, b)
+    plan.close()
+
+
 def test_tune_then_step(L):
     a, b = _twins(L, 1)
     plan = L.Plan(a)
