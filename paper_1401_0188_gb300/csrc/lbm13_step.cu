@@ -62,10 +62,12 @@ cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s)
     constexpr int R = sizeof(T) == 8 ? 1 : 2;
     constexpr int BY = 4;
     dim3 block(32, BY);
-    // A lattice of fewer than four R-row tiles per SM is latency-bound: one
-    // row per thread doubles the blocks in flight (same per-node arithmetic).
+    // A lattice of fewer than sixteen R-row tiles per SM (up to about 768^2,
+    // which lives in L2) is latency-bound: one row per thread doubles the
+    // blocks in flight (same per-node arithmetic).  From 1024^2 on, two rows
+    // per thread measured faster.
     const long long tiles2 = (long long)((a.nx + 31) / 32) * ((a.ny + BY * R - 1) / (BY * R));
-    if (R == 2 && tiles2 < 4 * 152) {
+    if (R == 2 && tiles2 < 16 * 152) {
         dim3 grid1((a.nx + 31) / 32, (a.ny + BY - 1) / BY);
         if (force)
             step_kernel<T, C, true, 1><<<grid1, block, 0, s>>>(a);
