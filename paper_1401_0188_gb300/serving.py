@@ -114,7 +114,9 @@ class Server:
     CPU tests of the admission logic pass a stand-in)."""
 
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
-                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13):
+                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config=(1, 4, 0, 2, 1)):
+        # plan_config: (R, BY, ctas_per_sm, order, groups) of the batched step
+        self.plan_config = tuple(plan_config)
         self.backend = backend
         self.precision = precision
         self.hbm_budget = hbm_budget
@@ -162,7 +164,7 @@ class Server:
                     if plan is not None:
                         plan.close()
                     plan = self.backend.Plan([a.lat for a in active])
-                    plan.set_config(1, 4, 0, 2, 1)
+                    plan.set_config(*self.plan_config)
                 plan.step(self.check_every)
                 res = plan.residual(raise_on_divergence=False)
             else:
