@@ -151,10 +151,10 @@ def traffic_record(tag):
     return profile_record("step_kernel_traffic.txt", tag)
 
 
-# FP64 FMA units: the nominal 1.25 TFLOP/s FP64 of a GB300 at its 2070 MHz
-# maximum SM clock is 2 FMA (4 flops) per SM per clock over 152 SMs.
-FP64_FMA_PER_SM_CLK = 2
-SMS = 152
+# Nominal FP64 rate of a GB300 (1.25 TFLOP/s at its 2070 MHz maximum SM
+# clock: 2 FMA per SM per clock over 152 SMs), reported beside the measured
+# rate as context only.
+FP64_NOMINAL_FMA_PER_S = 2 * 152 * 2070e6
 
 
 def cpu_baseline(steps_target_s=12.0, n=512):
@@ -424,12 +424,19 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
-        lbm13._check(L.lbm13_set_state(lat.handle, *ptrs), lat.handle)
+        lbm13._check(L.lbm13_set_state(lat.handle, *ptrs), lat.handle)  # returns after the upload
+        t1 = time.perf_counter()
         lat.step(args.steps)
-        lbm13._check(L.lbm13_moments(lat.handle, outp, mask), lat.handle)
-        dt = time.perf_counter() - t0
+        lat.synchronize()
+        t2 = time.perf_counter()
+        lbm13._check(L.lbm13_moments(lat.handle, outp, mask), lat.handle)  # returns after the download
+        t3 = time.perf_counter()
+        dt = t3 - t0
         e2e = {"value": aggregate_mlups(n * n, args.steps, max_over_ranks(dt, dev, world), world), "unit": UNIT,
                "h2d_bytes_per_step": 4 * 8 * n * n / args.steps, "d2h_bytes_per_step": 4 * 8 * n * n / args.steps,
+               "split_ms": {"upload_and_init": 1e3 * (t1 - t0), "steps": 1e3 * (t2 - t1),
+                            "readout_and_download": 1e3 * (t3 - t2)},
+               "copy_fraction": ((t1 - t0) + (t3 - t2)) / dt,
                "note": f"per job: upload (rho,ux,uy,T) from pinned host, {args.steps} steps, download the same 4 fields"}
         del host, out
     lat.close()
@@ -449,17 +456,22 @@ def run_ours(args):
                 "bytes_per_lu": 208, "hbm_gbs": 208 * n * n / s64 / 1e9,
                 "hbm_frac": 208 * n * n / s64 / 1e9 / peak}
         # bound by the FP64 pipe: FP64 instructions per node (DADD + DMUL +
-        # DFMA, counted by ncu on this kernel source) against the issue rate
+        # DFMA, counted by ncu on this kernel source) against the FP64
+        # instruction rate measured on this GPU by the library's FMA-chain
+        # probe, right after the step's timing (clocks sampled during both)
         ops = profile_record("step_kernel_fp64_ops.txt", "fp64_instr_per_node")
-        mhz = (clk.summary() or {}).get("sm_max_mhz") or 2070.0
-        peak_alu = FP64_FMA_PER_SM_CLK * SMS * mhz * 1e6 / 1e9
+        with Clocks(local) as clk64:
+            rate, probe_s = lbm13.fp64_fma_rate(1 << 16)
+        peak_alu = rate / 1e9
         fp64["roofline"] = {
-            "bound": "alu", "unit": "G FP64 instr/s", "peak": peak_alu,
+            "bound": "alu", "unit": "G FP64 instr/s", "peak": peak_alu, "peak_kind": "measured",
             "achieved": None if ops is None else ops * n * n / s64 / 1e9,
             "frac": None if ops is None else ops * n * n / s64 / 1e9 / peak_alu,
             "instr_per_node": ops,
-            "peak_basis": f"{FP64_FMA_PER_SM_CLK} FP64 FMA per SM per clock x {SMS} SMs x {mhz:.0f} MHz "
-                          "(nominal 1.25 TFLOP/s at 2070 MHz)"}
+            "peak_basis": f"lbm13_fp64_fma_rate: 8 independent FMA chains per thread, 8 blocks of 256 per SM, "
+                          f"{probe_s * 1e3:.1f} ms timed with CUDA events",
+            "peak_clocks": clk64.summary(),
+            "nominal_peak": FP64_NOMINAL_FMA_PER_S / 1e9}
         lat.close()
         del lat
         torch.cuda.empty_cache()

@@ -89,9 +89,9 @@ typedef struct {
     double T;
 } lbm13_wall;
 
-/* Wall density of the velocity+temperature walls.  Sec. 7 estimates it "by
- * extrapolation from values measured in the fluid": EXTRAPOLATE takes
- * 1.5 rho(first node) - 0.5 rho(second node).  Those walls are not mass-tight
+/* Wall density of the velocity+temperature walls.  Sec. 7 takes it from an
+ * extrapolation of the fluid's values without giving the rule; EXTRAPOLATE
+ * uses 1.5 rho(first node) - 0.5 rho(second node).  Those walls are not mass-tight
  * (mass drifts slowly through them, ~1e-8 per step per node in a cavity), so
  * ZERO_FLUX offers the density that makes the wall's net normal mass flux
  * zero, estimated from the outgoing populations; the total mass is then
@@ -374,33 +374,48 @@ int lbm13_plan_config(lbm13_plan_t p, int64_t out[9]);
  * 1 s since the last call (its tile was left unstepped). */
 int lbm13_plan_residual(lbm13_plan_t p, double *out);
 
+/* Measured FP64 instruction rate of the current device, the denominator of
+ * the FP64 time step's roofline (that step is bound by its FP64 pipe, not by
+ * HBM).  The paper has no counterpart.  Every SM runs 8 blocks of 256 threads,
+ * each thread 8 independent FMA chains of `iters` FMAs (iters in 1..2^24),
+ * timed with CUDA events after a warm-up launch on a stream of its own:
+ * *fma_per_s = FMAs retired per second, *seconds (may be NULL) the timed
+ * launch's duration.  LBM13_EINVAL for NULL fma_per_s or iters out of range,
+ * LBM13_ECUDA if a CUDA call fails. */
+int lbm13_fp64_fma_rate(int iters, double *fma_per_s, double *seconds);
+
 /* Largest lattice (nx * ny) that lbm13_totals_noalloc accepts. */
 #define LBM13_NOALLOC_MAX_NODES 67108864
 
 /* Conserved totals of the stored state without allocating anything.
  * The paper has no counterpart; this is a service for callers that cannot
- * allocate device memory when they need the totals: code running while a
- * stream is captured in global mode (cudaMalloc fails there and invalidates
- * the capture), serving loops whose device memory is all pre-reserved under a
- * fixed budget by another allocator, and callbacks that must not re-enter the
- * lattice's allocator.  lbm13_residual allocates on its first call; this call
- * never calls cudaMalloc, cudaFree or any allocating routine.
+ * allocate device memory at the moment they need the totals: a serving loop
+ * that has handed every byte of its HBM budget to lattices through another
+ * allocator (one more buffer would break the budget or fail), a latency-bound
+ * loop that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree may impose, and code running inside an allocator callback, which
+ * must not re-enter that allocator.  lbm13_residual allocates its reduction
+ * buffers on its first call; this call never calls cudaMalloc, cudaFree or
+ * any allocating routine.
  *
  * out is a caller-owned DEVICE buffer of 8 doubles, written in stream order on
  * the lattice's stream (the call returns before the work ends): 0 sum rho,
  * 1 sum j_x, 2 sum j_y, 3 sum E (stored post-collision moments, as
  * LBM13_R_MASS..LBM13_R_ENERGY of lbm13_residual), 4 number of non-finite
- * populations, 5 max |u|, 6 mean T, 7 nx * ny.
+ * populations, 5 max |u|, 6 mean T, 7 nx * ny.  The call reads the population
+ * buffer that holds the lattice's state when the call is made.
  *
  * Scratch: a file-scope device array of 256 KiB (4096 x 8 doubles) that every
  * GPU loading the library holds until the process exits; lattices of up to
  * LBM13_NOALLOC_MAX_NODES nodes fit (larger ones return LBM13_EINVAL).  The
- * first call on a device looks up that array's device address with the device
- * current; make that first call before any stream capture.  Every call reuses
- * the same array and each call's blocks overwrite their rows before they are
- * read, so nothing needs clearing; calls whose work overlaps on the GPU (other
- * streams, other lattices) race on it.  Returns LBM13_EINVAL for a NULL
- * argument or an oversized lattice, LBM13_ECUDA if a launch fails. */
+ * first call on a device (and the first after that device's context was
+ * replaced, e.g. by cudaDeviceReset) looks up that array's device address with
+ * the device current; make that first call before any stream capture.  Every
+ * call reuses the same array and each call's blocks overwrite their rows before
+ * they are read, so nothing needs clearing; calls whose work overlaps on the
+ * GPU (other streams, other lattices) race on it.  Returns LBM13_EINVAL for a
+ * NULL argument or an oversized lattice, LBM13_ECUDA if the lattice's device
+ * cannot be made current or one of the call's own launches fails. */
 int lbm13_totals_noalloc(lbm13_t h, double *out);
 
 #ifdef __cplusplus

@@ -400,7 +400,7 @@ int reduce_blocks(int nx, int ny)
 {
     const long long n = (long long)nx * ny;
     long long b = (n + kReduceThreads - 1) / kReduceThreads;
-    const long long cap = 152 * 8;  // a few waves of the 152 SMs
+    const long long cap = 8LL * device_sm_count();  // eight blocks per SM
     return int(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 

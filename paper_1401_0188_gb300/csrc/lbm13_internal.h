@@ -124,6 +124,10 @@ struct ReadArgs {
     double heat;  // energy source q: T is read half-way, (p* - q/2)/rho
 };
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 1 if the query fails, so that callers still size a valid grid).
+int device_sm_count();
+
 // Launchers (return the cudaError_t of the launch).
 template <typename T, typename C>
 cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s);

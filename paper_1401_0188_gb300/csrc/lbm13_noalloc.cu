@@ -2,14 +2,16 @@
 //
 // lbm13_residual allocates its reduction buffers (six doubles per node plus
 // block partials) through the lattice's allocator on its first call.  Some
-// callers cannot allocate at the point where they need the totals: code that
-// runs while a stream is being captured in global mode (cudaMalloc fails
-// there and breaks the capture), serving loops that keep every byte of device
-// memory under a fixed budget owned by another allocator, and callbacks that
-// must not re-enter the allocator.  lbm13_totals_noalloc serves them: the same
-// deterministic FP64 sums, with the block partials in a fixed file-scope
+// callers cannot allocate at the point where they need the totals: a serving
+// loop whose device memory is all handed to lattices under a fixed budget by
+// another allocator, a latency-bound loop that cannot take the device-wide
+// synchronisation cudaMalloc/cudaFree may impose, and code inside an allocator
+// callback that must not re-enter it.  lbm13_totals_noalloc serves them: the
+// same deterministic FP64 sums, with the block partials in a fixed file-scope
 // device array instead of allocated memory.
 #include <mutex>
+
+#include <cuda.h>  // CUcontext (the type only: the two driver calls are fetched through the runtime)
 
 #include "../../include/lbm13.h"
 #include "lbm13_internal.h"
@@ -144,31 +146,74 @@ __global__ void __launch_bounds__(kThreads) totals_final(const double *partials,
     }
 }
 
-// Device address of g_partials, looked up once per device with that device
-// current (in host code the name g_partials is only a host-side stand-in).
+// Device address of g_partials, looked up with the device current (in host
+// code the name g_partials is only a host-side stand-in) once per device and
+// context: the cache is keyed by the context's unique ID, so a context that
+// replaced the old one (after cudaDeviceReset) gets its own lookup.
 constexpr int kMaxDevices = 64;
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double *addr;
+};
 std::mutex g_mutex;
-double *g_addr[kMaxDevices] = {};
+ScratchEntry g_cache[kMaxDevices] = {};
 
+using CtxGetCurrent = CUresult (*)(CUcontext *);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long *);
+
+template <typename Fn>
+Fn driver_entry(const char *name)
+{
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return reinterpret_cast<Fn>(ptr);
+    return nullptr;
+}
+
+// Unique ID of the current context (0 if the driver cannot tell).
+unsigned long long current_context_id()
+{
+    static const CtxGetCurrent get_current = driver_entry<CtxGetCurrent>("cuCtxGetCurrent");
+    static const CtxGetId get_id = driver_entry<CtxGetId>("cuCtxGetId");
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// The caller has made `device` current.
 cudaError_t scratch_address(int device, double **out)
 {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[device]) {
+    ScratchEntry &c = g_cache[device];
+    if (!c.addr || id == 0 || c.ctx_id != id) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess) return e;
-        g_addr[device] = static_cast<double *>(p);
+        c.addr = static_cast<double *>(p);
+        c.ctx_id = id;
     }
-    *out = g_addr[device];
+    *out = c.addr;
     return cudaSuccess;
 }
 
+// Makes `dev` current for the call and restores the caller's device after it;
+// ok is false when the device could not be made current.
 struct Guard {
     int prev = -1;
+    bool ok = false;
     explicit Guard(int dev)
     {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            return;
+        }
+        ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
     }
     ~Guard()
     {
@@ -176,6 +221,17 @@ struct Guard {
         if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
     }
 };
+
+template <typename T>
+cudaError_t launch_totals(const StateView &v, int nblocks, double *scratch)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(nblocks));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = v.stream;
+    return cudaLaunchKernelEx(&cfg, totals_kernel<T>, static_cast<const T *>(v.f), v.nx, v.ny, v.pitch, v.plane, v.E0,
+                              v.gx, v.gy, v.rho_ref, v.heat, scratch);
+}
 
 } // namespace
 
@@ -186,15 +242,19 @@ extern "C" int lbm13_totals_noalloc(lbm13_t h, double *out)
     const long long n = (long long)v.nx * v.ny;
     if (n > LBM13_NOALLOC_MAX_NODES) return LBM13_EINVAL;
     Guard g(v.device);
+    if (!g.ok) return LBM13_ECUDA;
     double *scratch = nullptr;
     if (scratch_address(v.device, &scratch) != cudaSuccess) return LBM13_ECUDA;
     const int nblocks = int((n + kNodesPerBlock - 1) / kNodesPerBlock);
-    if (v.precision == LBM13_FP64)
-        totals_kernel<double><<<nblocks, kThreads, 0, v.stream>>>(static_cast<const double *>(v.f), v.nx, v.ny, v.pitch,
-                                                                   v.plane, v.E0, v.gx, v.gy, v.rho_ref, v.heat, scratch);
-    else
-        totals_kernel<float><<<nblocks, kThreads, 0, v.stream>>>(static_cast<const float *>(v.f), v.nx, v.ny, v.pitch,
-                                                                  v.plane, v.E0, v.gx, v.gy, v.rho_ref, v.heat, scratch);
-    totals_final<<<1, kThreads, 0, v.stream>>>(scratch, nblocks, n, v.E0, out);
-    return cudaGetLastError() == cudaSuccess ? LBM13_OK : LBM13_ECUDA;
+    // each launch's own status (not the thread's last-error slot, which may
+    // hold an unrelated earlier failure)
+    cudaError_t e = v.precision == LBM13_FP64 ? launch_totals<double>(v, nblocks, scratch)
+                                              : launch_totals<float>(v, nblocks, scratch);
+    if (e != cudaSuccess) return LBM13_ECUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = v.stream;
+    e = cudaLaunchKernelEx(&cfg, totals_final, static_cast<const double *>(scratch), nblocks, n, v.E0, out);
+    return e == cudaSuccess ? LBM13_OK : LBM13_ECUDA;
 }

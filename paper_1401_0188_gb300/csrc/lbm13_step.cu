@@ -31,6 +31,8 @@
 // to a wall evaluate its state at their own position and add the wall
 // correction, a quadratic in (rho_w, E_w) whose coefficients the host computes
 // once per lattice.
+#include <atomic>
+
 #include "lbm13_internal.h"
 
 // Each launch reads only what earlier launches wrote: the read-only path.
@@ -56,18 +58,34 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 && !(Force && R == 2) ? 6 
 
 } // namespace
 
+int device_sm_count()
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kMaxDevices) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 template <typename T, typename C>
 cudaError_t launch_step(const StepArgs<T, C> &a, bool force, cudaStream_t s)
 {
     constexpr int R = sizeof(T) == 8 ? 1 : 2;
     constexpr int BY = 4;
     dim3 block(32, BY);
-    // A lattice of fewer than sixteen R-row tiles per SM (up to about 768^2,
-    // which lives in L2) is latency-bound: one row per thread doubles the
+    // A lattice of fewer than sixteen R-row tiles per SM (up to about 768^2
+    // on 152 SMs, which lives in L2) is latency-bound: one row per thread doubles the
     // blocks in flight (same per-node arithmetic).  From 1024^2 on, two rows
     // per thread measured faster.
     const long long tiles2 = (long long)((a.nx + 31) / 32) * ((a.ny + BY * R - 1) / (BY * R));
-    if (R == 2 && tiles2 < 16 * 152) {
+    if (R == 2 && tiles2 < 16LL * device_sm_count()) {
         dim3 grid1((a.nx + 31) / 32, (a.ny + BY - 1) / BY);
         if (force)
             step_kernel<T, C, true, 1><<<grid1, block, 0, s>>>(a);

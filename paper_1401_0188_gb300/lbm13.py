@@ -38,7 +38,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
            "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
-           "lbm13_plan_tma_check")
+           "lbm13_plan_tma_check", "lbm13_fp64_fma_rate")
 
 
 class Lbm13Error(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
         "lbm13_time": (i64, [vp]),
         "lbm13_synchronize": (C.c_int, [vp]),
         "lbm13_totals_noalloc": (C.c_int, [vp, vp]),
+        "lbm13_fp64_fma_rate": (C.c_int, [C.c_int, dp, dp]),
         "lbm13_plan_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(Allocator), vp, C.POINTER(vp)]),
         "lbm13_plan_destroy": (None, [vp]),
         "lbm13_plan_last_error": (C.c_char_p, [vp]),
@@ -182,6 +183,14 @@ def barrier_check(blocks, extra_blocks, timeout_s):
     out = C.c_int(0)
     _check(lib().lbm13_barrier_check(int(blocks), int(extra_blocks), float(timeout_s), C.byref(out)))
     return bool(out.value)
+
+
+def fp64_fma_rate(iters=1 << 15):
+    """Measured FP64 FMAs per second of the current device, and the timed
+    launch's duration in seconds."""
+    rate, sec = C.c_double(), C.c_double()
+    _check(lib().lbm13_fp64_fma_rate(int(iters), C.byref(rate), C.byref(sec)))
+    return rate.value, sec.value
 
 
 def lbm13_version():
