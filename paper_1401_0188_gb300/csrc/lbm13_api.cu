@@ -1086,6 +1086,21 @@ bool encode_lattice_map(lbm13_t h, const void *buf, CUtensorMap *m)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same buffer ordered (x, plane, y) for the ring-staged strips: a box of
+// kRingX x 13 x kRingRows lands in shared memory as [row][plane][column].
+bool encode_ring_map(lbm13_t h, const void *buf, CUtensorMap *m)
+{
+    const EncodeTiled fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(h->nx), cuuint64_t(Q), cuuint64_t(h->ny)};
+    const cuuint64_t strides[2] = {cuuint64_t(h->plane) * 4u, cuuint64_t(h->pitch) * 4u};
+    const cuuint32_t box[3] = {cuuint32_t(kRingX), cuuint32_t(Q), cuuint32_t(kRingRows)};
+    const cuuint32_t step[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(buf), dims, strides, box, step,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor maps of every lattice of an FP32 plan for both parities (lattices
 // narrower than 64 columns or lower than the box keep global loads).
 int plan_upload_maps(lbm13_plan_t p)
@@ -1097,6 +1112,9 @@ int plan_upload_maps(lbm13_plan_t p)
         const int cur = p->cur0[i];
         host[i].use = h->nx >= 64 && h->ny >= kTmaY && encode_lattice_map(h, h->buf[cur], &host[i].map[0]) &&
                       encode_lattice_map(h, h->buf[cur ^ 1], &host[i].map[1]);
+        host[i].ring_use = h->nx >= kRingW && h->ny >= kRingRows &&
+                           encode_ring_map(h, h->buf[cur], &host[i].ring[0]) &&
+                           encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring[1]);
     }
     const size_t bytes = host.size() * sizeof(LatticeMaps);
     if (!p->maps || p->maps_bytes < bytes) {
@@ -1153,14 +1171,19 @@ int plan_upload_descs(lbm13_plan_t p)
 // (tile row << 16) | tile column (both below 2^15 within the lattice limits),
 // in one of three orders: 0 lattice by lattice, 1 round robin across
 // lattices, 2 largest lattice first.
+bool plan_is_ring(const lbm13_plan *p) { return p->R == 0 && p->BY == 8; }
+
 int plan_build_work(lbm13_plan_t p)
 {
-    const int rows = p->R * p->BY * p->groups;
+    // ring tiles: strips of kRingW columns x groups 4-row groups
+    const bool ring = plan_is_ring(p);
+    const int rows = ring ? kRingRows * p->groups : p->R * p->BY * p->groups;
+    const int cols = ring ? kRingW : 32;
     const size_t L = p->lats.size();
     std::vector<std::vector<int2>> per(L);
     for (size_t i = 0; i < L; ++i) {
         lbm13_t h = p->lats[i];
-        const int tx = (h->nx + 31) / 32, ty = (h->ny + rows - 1) / rows;
+        const int tx = (h->nx + cols - 1) / cols, ty = (h->ny + rows - 1) / rows;
         per[i].reserve(size_t(tx) * ty);
         for (int y = 0; y < ty; ++y)
             for (int x = 0; x < tx; ++x) per[i].push_back(make_int2(int(i), (y << 16) | x));
@@ -1198,6 +1221,12 @@ int plan_build_work(lbm13_plan_t p)
 
 cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
 {
+    if (plan_is_ring(p)) {
+        if (p->precision == LBM13_FP64 || !p->maps || !p->tma_err) return cudaErrorInvalidValue;
+        return launch_batch_ring(static_cast<const BatchDesc<float, float> *>(p->desc),
+                                 static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
+                                 p->ntiles, parity, p->groups, p->tma_err, s);
+    }
     if (p->precision != LBM13_FP64 && p->R == 4 && p->BY == 4 && p->grid >= p->ntiles && p->maps && p->tma_err)
         return launch_batch_tma(static_cast<const BatchDesc<float, float> *>(p->desc),
                                 static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
@@ -1331,6 +1360,8 @@ int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int or
     if (!batch_shape_supported(R, BY) || order < 0 || order > 2 || ctas_per_sm < 0 || ctas_per_sm > 64 ||
         groups < 1 || groups > 64)
         return pfail(p, LBM13_EINVAL, "unsupported tile shape, order, CTA count or row groups");
+    if (R == 0 && p->precision == LBM13_FP64)
+        return pfail(p, LBM13_EINVAL, "the ring-staged tile shape (R = 0, BY = 8) is FP32 only");
     DeviceGuard g(p->device);
     p->R = R;
     p->BY = BY;
@@ -1344,16 +1375,23 @@ int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *ti
 {
     if (!p || !timed_out || !(timeout_s >= 1e-3 && timeout_s <= 2.0))
         return pfail(p, LBM13_EINVAL, "NULL argument or timeout_s outside [1e-3, 2]");
-    if (p->precision == LBM13_FP64 || p->R != 4 || p->BY != 4 || p->grid < p->ntiles || !p->maps || !p->tma_err)
-        return pfail(p, LBM13_EINVAL, "the plan is not on the staged FP32 tiles (R = 4, BY = 4, one CTA per tile)");
+    const bool ring = plan_is_ring(p);
+    if (p->precision == LBM13_FP64 || !p->maps || !p->tma_err ||
+        !(ring || (p->R == 4 && p->BY == 4 && p->grid >= p->ntiles)))
+        return pfail(p, LBM13_EINVAL,
+                     "the plan is not on staged FP32 tiles (R = 4, BY = 4, one CTA per tile; or the ring, R = 0, BY = 8)");
     DeviceGuard g(p->device);
     int rc = plan_sync_parity(p);
     if (rc != LBM13_OK) return rc;
     unsigned word = 0;
-    cudaError_t e = launch_batch_tma(static_cast<const BatchDesc<float, float> *>(p->desc),
-                                     static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
-                                     p->ntiles, p->parity, p->groups, p->tma_err, p->stream, withhold ? 0 : 1,
-                                     (unsigned long long)(timeout_s * 1e9));
+    const auto *descs = static_cast<const BatchDesc<float, float> *>(p->desc);
+    const auto *maps = static_cast<const LatticeMaps *>(p->maps);
+    const auto *work = static_cast<const int2 *>(p->work);
+    const unsigned long long wait_ns = (unsigned long long)(timeout_s * 1e9);
+    cudaError_t e = ring ? launch_batch_ring(descs, maps, work, p->ntiles, p->parity, p->groups, p->tma_err, p->stream,
+                                             withhold ? 0 : 1, wait_ns)
+                         : launch_batch_tma(descs, maps, work, p->ntiles, p->parity, p->groups, p->tma_err, p->stream,
+                                            withhold ? 0 : 1, wait_ns);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e == cudaSuccess) e = cudaMemcpy(&word, p->tma_err, sizeof word, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(p->tma_err, 0, sizeof word);
@@ -1426,47 +1464,55 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
     Range range_("lbm13_plan_tune");
     if (!p || steps_per_candidate < 1) return pfail(p, LBM13_EINVAL, "NULL plan or steps_per_candidate < 1");
     DeviceGuard g(p->device);
+    struct Cand {
+        int R, BY, ctas, groups, order;
+    };
+    std::vector<Cand> cands;
     static const int shapes[][2] = {{1, 4}, {2, 4}, {4, 4}, {2, 2}, {1, 8}};
     static const int ctas[] = {0, 4, 8, 16};
     static const int groups[] = {1, 4, 16};
+    for (const auto &sh : shapes)
+        for (int c : ctas)
+            for (int gr : groups)
+                for (int o = 0; o < 3; ++o) cands.push_back({sh[0], sh[1], c, gr, o});
+    // ring-staged strips (FP32): one block per strip segment of 4 groups rows
+    static const int ring_groups[] = {8, 16, 32, 64};
+    if (p->precision != LBM13_FP64)
+        for (int gr : ring_groups)
+            for (int o = 0; o < 3; ++o) cands.push_back({0, 8, 0, gr, o});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return pfail(p, LBM13_ECUDA, "cudaEventCreate");
     double best = 1e300;
-    int bR = p->R, bBY = p->BY, bC = p->ctas, bO = p->order, bG = p->groups, rc = LBM13_OK;
+    Cand b = {p->R, p->BY, p->ctas, p->groups, p->order};
+    int rc = LBM13_OK;
     p->tried = 0;
-    for (const auto &sh : shapes) {
-        for (int c : ctas) {
-            for (int gr : groups) {
-                for (int o = 0; o < 3 && rc == LBM13_OK; ++o) {
-                    p->R = sh[0];
-                    p->BY = sh[1];
-                    p->ctas = c;
-                    p->order = o;
-                    p->groups = gr;
-                    if ((rc = plan_build_work(p)) != LBM13_OK) break;
-                    if ((rc = plan_steps(p, 1)) != LBM13_OK) break;  // warm-up
-                    cudaEventRecord(e0, p->stream);
-                    if ((rc = plan_steps(p, steps_per_candidate)) != LBM13_OK) break;
-                    cudaEventRecord(e1, p->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = pfail(p, LBM13_ECUDA, "tuning event"); break; }
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    const double per = double(ms) / steps_per_candidate;
-                    ++p->tried;
-                    if (per < best) { best = per; bR = sh[0]; bBY = sh[1]; bC = c; bO = o; bG = gr; }
-                }
-            }
-        }
+    for (const Cand &c : cands) {
+        p->R = c.R;
+        p->BY = c.BY;
+        p->ctas = c.ctas;
+        p->order = c.order;
+        p->groups = c.groups;
+        if ((rc = plan_build_work(p)) != LBM13_OK) break;
+        if ((rc = plan_steps(p, 1)) != LBM13_OK) break;  // warm-up
+        cudaEventRecord(e0, p->stream);
+        if ((rc = plan_steps(p, steps_per_candidate)) != LBM13_OK) break;
+        cudaEventRecord(e1, p->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = pfail(p, LBM13_ECUDA, "tuning event"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / steps_per_candidate;
+        ++p->tried;
+        if (per < best) { best = per; b = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LBM13_OK) return rc;
-    p->R = bR;
-    p->BY = bBY;
-    p->ctas = bC;
-    p->order = bO;
-    p->groups = bG;
+    p->R = b.R;
+    p->BY = b.BY;
+    p->ctas = b.ctas;
+    p->order = b.order;
+    p->groups = b.groups;
     if ((rc = plan_build_work(p)) != LBM13_OK) return rc;
     if (best_ms_per_step) *best_ms_per_step = best;
     return LBM13_OK;

@@ -134,18 +134,25 @@ __device__ __forceinline__ void tma_slab(unsigned dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Wait for phase `phase` of the barrier to complete, for at most wait_ns.
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned phase)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `phase` of the barrier to complete, for at most wait_ns (the
+// global timer is read only once the first try has failed).
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, unsigned long long wait_ns)
 {
+    if (mbar_try(bar, phase)) return true;
     const unsigned long long end = tma_clock() + wait_ns;
     for (;;) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(bar, phase)) return true;
         if (tma_clock() > end) return false;
     }
 }
@@ -279,6 +286,258 @@ __global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float
     }
 }
 
+// ------------------------------------------------- ring-staged strips
+//
+// FP32 only.  A block of eight warps steps a strip of 64 columns of one
+// lattice over `groups` 4-row output groups (rows yb .. yb + 4 groups - 1).
+// Input chunk k (rows yb - 2 + 4k .. yb + 1 + 4k, columns x0 - 4 .. x0 + 67,
+// all 13 planes) arrives by one tensor copy in ring slot k % kRingSlots, laid
+// out [row][plane][column], so input row r (relative to yb - 2) sits in ring
+// row r & 15.  The first lane of warp 0 is also the producer: it issues the
+// first kRingSlots chunks at once, then, at the top of each group g >= 1,
+// chunk g + 3 into the slot of chunk g - 1 once every warp has released that
+// chunk.  Warp w steps row yb + 4g + (w & 3) of output group g in the column
+// half w >> 2, pulling its 13 populations from chunks g and g + 1, and
+// releases chunk g when the group is done (group g + 1 reads chunks g + 1 and
+// g + 2).  The lattice's collision coefficients live in registers for the
+// whole strip; every warp runs the same code (the row within the group only
+// moves five ring-row addresses), and this phase makes no out-of-line call:
+// it steps only the nodes at least two links from every edge.  The block's
+// edge nodes come first, through process_column (periodic wraps and wall
+// rules) with global loads that overlap the first chunks' copies, so the
+// results are bit-identical to the other kernels.
+
+__device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// One chunk: the box at (column x, plane 0, row y) of a map ordered (x, plane, y).
+__device__ __forceinline__ void ring_chunk(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRingBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(0), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Chunk k of the strip into its slot (the producer lane).
+__device__ __forceinline__ void ring_issue(const CUtensorMap *map, unsigned st0, unsigned full0, int x0, int yb, int k)
+{
+    const int slot = k % kRingSlots;
+    ring_chunk(st0 + unsigned(slot) * kRingBytes, map, x0 - 4, yb - 2 + kRingRows * k, full0 + 8u * slot);
+}
+
+// Before the producer's warp leaves (normally or after a wait ran out), the
+// copies issued into slots that no later copy re-armed must have landed, so
+// that none lands in the block's shared memory after the block has left.
+__device__ __forceinline__ void ring_drain(unsigned full0, int issued, unsigned long long wait_ns)
+{
+    for (int j = issued > kRingSlots ? issued - kRingSlots : 0; j < issued; ++j)
+        mbar_wait(full0 + 8u * (j % kRingSlots), unsigned((j / kRingSlots) & 1), wait_ns);
+}
+
+// The 13 populations of a node from the staged rows: rb[d] is the address of
+// ring row (input row of the node minus d) at the node's column (d = v_y in
+// -2 .. 2, index d + 2); link j reads plane j of ring row rb[v_y] at column
+// offset -v_x.
+__device__ __forceinline__ void ring_pull(const float *const rb[5], float f[Q])
+{
+#pragma unroll
+    for (int j = 0; j < Q; ++j) f[j] = rb[cvy(j) + 2][j * kRingX - cvx(j)];
+}
+
+// Staged phase of a consumer warp: the nodes of its row that lie at least two
+// links from every edge, from the staged rows, with the coefficients in
+// registers and no out-of-line call.  Returns false after a wait ran out.
+template <bool Force>
+__device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage, unsigned full0, unsigned empty0,
+                             int x0, int yb, int ngroups, int wr, int half, const CUtensorMap *map, int producer,
+                             unsigned *err, unsigned long long wait_ns)
+{
+    const Coef<float> k = a.k;  // in registers for the whole strip
+    const int lane = threadIdx.x & 31;
+    const int nchunks = ngroups + 1;
+    const unsigned st0 = static_cast<unsigned>(__cvta_generic_to_shared(stage));
+    int issued = producer ? min(nchunks, kRingSlots) : 0;  // the first ones went out with the set-up
+    const int nx = a.nx, ny = a.ny;
+    const int x = x0 + 32 * half + lane;
+    const float *const colp = stage + 32 * half + lane + 4;  // the node's column in ring row 0
+    const bool xin = x >= 2 && x < nx - 2;
+    float *const fout = a.fout;
+    const long long pitch = a.pitch, plane = a.plane;
+    for (int g = 0; g < ngroups; ++g) {
+        bool ok = true;
+        if (producer && lane == 0 && g >= 1 && issued < nchunks) {
+            // chunk g + 3 takes the slot of chunk g - 1: wait until every warp
+            // has released that chunk
+            const int c = g - 1;
+            ok = mbar_wait(empty0 + 8u * (c % kRingSlots), unsigned((c / kRingSlots) & 1), wait_ns);
+            if (ok) ring_issue(map, st0, full0, x0, yb, issued++);
+        }
+        if (g == 0) ok = ok && mbar_wait(full0, 0u, wait_ns);
+        {
+            const int c = g + 1;
+            ok = ok && mbar_wait(full0 + 8u * (c % kRingSlots), unsigned((c / kRingSlots) & 1), wait_ns);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicOr(err, 1u);
+                if (producer) ring_drain(full0, issued, wait_ns);
+            }
+            return false;
+        }
+        const int y = yb + kRingRows * g + wr;
+        if (xin && y >= 2 && y <= ny - 3) {
+            // input row of the node relative to yb - 2
+            const int r = kRingRows * g + wr + 2;
+            const float *rb[5];
+#pragma unroll
+            for (int d = -2; d <= 2; ++d) rb[d + 2] = colp + ((r - d) & (kRingRowsTotal - 1)) * kRingRowFloats;
+            float f[Q];
+            ring_pull(rb, f);
+            collide<Force>(f, k);
+#ifdef LBM13_DEBUG
+            store(a, x, y, f);
+#else
+            float *p = fout + (long long)y * pitch + x;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) p[(long long)j * plane] = f[j];
+#endif
+        }
+        // chunk g is needed by no later group: release its slot
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8u * (g % kRingSlots));
+    }
+    if (producer && lane == 0) ring_drain(full0, issued, wait_ns);
+    return true;
+}
+
+// Edge phase of the consumers: the nodes of the block's strip segment within two
+// links of an edge (rows 0, 1, ny-2, ny-1 across the strip; columns 0, 1,
+// nx-2, nx-1 in between), each through process_column with global loads (the
+// periodic wraps and the wall rules).  Every warp runs the same number of
+// iterations; lanes without a node pass x = nx, which neither loads out of the
+// lattice nor stores.
+template <bool Force>
+__device__ void ring_edges(const StepArgs<float, float> &a, int x0, int yb, int ngroups, int ctid, float *slot)
+{
+    constexpr int kT = 32 * kRingConsumers;
+    const int nx = a.nx, ny = a.ny;
+    const int y_end = min(ny, yb + kRingRows * ngroups), x_end = min(nx, x0 + kRingW);
+    int er[4], ec[4], nr = 0, nc = 0;
+    const int cy[4] = {0, 1, ny - 2, ny - 1}, cx[4] = {0, 1, nx - 2, nx - 1};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        bool dup_r = false, dup_c = false;
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            dup_r = dup_r || cy[j] == cy[i];
+            dup_c = dup_c || cx[j] == cx[i];
+        }
+        if (!dup_r && cy[i] >= yb && cy[i] < y_end && cy[i] >= 0) er[nr++] = cy[i];
+        if (!dup_c && cx[i] >= x0 && cx[i] < x_end && cx[i] >= 0) ec[nc++] = cx[i];
+    }
+    // edge rows: 64 columns each, a warp on 32 consecutive columns of one row
+    for (int i = ctid; i < nr * kRingW; i += kT) {
+        const int r = i / kRingW, x = x0 + i % kRingW;
+        process_column<float, float, Force, 1>(a, x < nx ? x : nx, er[r], slot);
+    }
+    // edge columns between the edge rows
+    const int ylo = max(yb, 2), yhi = min(y_end, ny - 2);
+    const int n = nc * max(0, yhi - ylo);
+    const int nround = (n + 31) & ~31;
+    for (int i = ctid; i < nround; i += kT) {
+        const bool have = i < n;
+        const int x = have ? ec[i % nc] : nx;
+        const int y = have ? ylo + i / nc : ylo;
+        process_column<float, float, Force, 1>(a, x, y, slot);
+    }
+}
+
+template <bool Force>
+__device__ __forceinline__ void ring_consume_row(int wr, const StepArgs<float, float> &a, const float *stage,
+                                                 unsigned full0, unsigned empty0, int x0, int yb, int ngroups,
+                                                 int half, const CUtensorMap *map, int producer, float *slot,
+                                                 unsigned *err, unsigned long long wait_ns)
+{
+    // the edge nodes first: their global loads overlap the first chunks' copies
+    ring_edges<Force>(a, x0, yb, ngroups, int(threadIdx.x), slot);
+    ring_consume<Force>(a, stage, full0, empty0, x0, yb, ngroups, wr, half, map, producer, err, wait_ns);
+}
+
+__global__ void __launch_bounds__(kRingThreads, 2) batch_ring_kernel(const BatchDesc<float, float> *__restrict__ descs,
+                                                                     const LatticeMaps *__restrict__ maps,
+                                                                     const int2 *__restrict__ work, int parity,
+                                                                     int groups, unsigned *err, int issue,
+                                                                     unsigned long long wait_ns)
+{
+    extern __shared__ __align__(128) unsigned char ring_smem[];
+    __shared__ StepArgs<float, float> sa;
+    __shared__ __align__(8) unsigned long long bars[2 * kRingSlots];  // full[slots], empty[slots]
+    __shared__ int s_force, s_use;
+    constexpr int kWords = int(sizeof(StepArgs<float, float>) / 16);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int2 w = __ldg(work + blockIdx.x);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
+        int4 *dst = reinterpret_cast<int4 *>(&sa);
+        for (int i = tid; i < kWords; i += kRingThreads) dst[i] = __ldg(src + i);
+    }
+    const unsigned full0 = static_cast<unsigned>(__cvta_generic_to_shared(&bars[0]));
+    const unsigned empty0 = full0 + 8u * kRingSlots;
+    if (tid == 0) {
+        s_force = descs[w.x].force;
+        s_use = maps[w.x].ring_use;
+        for (int i = 0; i < kRingSlots; ++i) {
+            mbar_init_count(full0 + 8u * i, 1u);
+            mbar_init_count(empty0 + 8u * i, unsigned(kRingConsumers));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int x0 = (w.y & 0xffff) * kRingW;
+    const int yb = (w.y >> 16) * groups * kRingRows;
+    const int ny = sa.ny;
+    const int ngroups = min(groups, (ny - yb + kRingRows - 1) / kRingRows);
+    float *stage = reinterpret_cast<float *>(ring_smem);
+    float *slots = stage + kRingSlots * kRingChunk;
+    if (!s_use) {
+        // a lattice without a ring tensor map: the warps step it through
+        // global loads, one row per warp and group
+        const int x = x0 + 32 * (warp >> 2) + (tid & 31);
+        for (int g = 0; g < ngroups; ++g) {
+            const int y = yb + kRingRows * g + (warp & 3);
+            if (y >= ny) break;
+            if (s_force)
+                process_column<float, float, true, 1>(sa, x, y, slots + tid * Q);
+            else
+                process_column<float, float, false, 1>(sa, x, y, slots + tid * Q);
+        }
+        return;
+    }
+    const CUtensorMap *map = &maps[w.x].ring[parity];
+    const int producer = warp == 0 && issue;
+    if (producer && (tid & 31) == 0) {
+        const unsigned st0 = static_cast<unsigned>(__cvta_generic_to_shared(stage));
+        for (int k = 0; k < ngroups + 1 && k < kRingSlots; ++k) ring_issue(map, st0, full0, x0, yb, k);
+    }
+    if (s_force)
+        ring_consume_row<true>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
+                               slots + tid * Q, err, wait_ns);
+    else
+        ring_consume_row<false>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
+                                slots + tid * Q, err, wait_ns);
+}
+
 template <typename T, typename C, int R, int BY>
 cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int groups,
                             int grid, cudaStream_t s)
@@ -295,7 +554,7 @@ cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int 
 bool batch_shape_supported(int R, int BY)
 {
     return (R == 1 && BY == 4) || (R == 2 && BY == 4) || (R == 4 && BY == 4) || (R == 2 && BY == 2) ||
-           (R == 1 && BY == 8);
+           (R == 1 && BY == 8) || (R == 0 && BY == 8);
 }
 
 template <typename T, typename C>
@@ -331,6 +590,30 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
         raised.fetch_or(bit);
     }
     batch_tma_kernel<<<ntiles, dim3(32, 4), kTmaSmem, s>>>(descs, maps, work, parity, groups, err, issue, wait_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ring(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
+                              int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue,
+                              unsigned long long wait_ns)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (groups < 1) return cudaErrorInvalidValue;
+    static std::atomic<unsigned long long> raised{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(raised.load() & bit)) {
+        e = cudaFuncSetAttribute(batch_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem);
+        // two blocks per SM need the largest shared-memory carveout
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_ring_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
+        if (e != cudaSuccess) return e;
+        raised.fetch_or(bit);
+    }
+    batch_ring_kernel<<<ntiles, kRingThreads, kRingSmem, s>>>(descs, maps, work, parity, groups, err, issue, wait_ns);
     return cudaGetLastError();
 }
 

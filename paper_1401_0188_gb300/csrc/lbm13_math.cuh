@@ -17,6 +17,8 @@
 // or FMAs each way instead of 2 x 169.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #define LBM13_HD __host__ __device__ __forceinline__
@@ -183,6 +185,46 @@ LBM13_HD double recip_uu(double x)
 }
 LBM13_HD float recip_uu(float x) { return 1.0f / x; }
 
+// Explicitly rounded products for the collision.  Every product in collide
+// is written as rn_mul (never merged with an addition) or rn_fma (one
+// rounding), so the compiler neither contracts nor splits any of them: the
+// collision rounds identically in every kernel that inlines it, wherever that
+// kernel holds the coefficients (kernel parameters, shared memory or
+// registers).  Sums need no wrapper: a lone addition cannot be contracted and
+// nothing is reassociated.
+LBM13_HD float rn_mul(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+LBM13_HD double rn_mul(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+LBM13_HD float rn_fma(float a, float b, float c)
+{
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+LBM13_HD double rn_fma(double a, double b, double c)
+{
+#ifdef __CUDA_ARCH__
+    return __fma_rn(a, b, c);
+#else
+    return fma(a, b, c);
+#endif
+}
+
 // One collision in place (deviation form).  Equilibria of Sec. 2, Eq.
 // (d2q13-moments-equil) at j + F/2 and E + 13 q; the nine non-conserved
 // moments relax as m* = m + s (m_eq - m); j* = j + F and
@@ -205,60 +247,61 @@ LBM13_HD void collide(C f[Q], const Coef<C> &k)
     const C dm = b5 - b6, dp = b5 + b6;
     // conserved and odd moments (deviations)
     const C drho = f[0] + S1 + S5 + S9;
-    const C dE = C(-28) * f[0] + C(-15) * S1 + C(-2) * S5 + C(24) * S9;
-    const C jx = b1 + dm + C(2) * b9;
-    const C jy = b2 + dp + C(2) * b10;
-    const C qx = C(-2) * b1 - dm + C(2) * b9;
-    const C qy = C(-2) * b2 - dp + C(2) * b10;
-    const C rx = C(4) * b1 + C(-3) * dm + b9;
-    const C ry = C(4) * b2 + C(-3) * dp + b10;
+    const C dE = rn_fma(C(24), S9, rn_fma(C(-2), S5, rn_fma(C(-15), S1, rn_mul(C(-28), f[0]))));
+    const C jx = rn_fma(C(2), b9, b1 + dm);
+    const C jy = rn_fma(C(2), b10, b2 + dp);
+    const C qx = rn_fma(C(2), b9, rn_fma(C(-2), b1, -dm));
+    const C qy = rn_fma(C(2), b10, rn_fma(C(-2), b2, -dp));
+    const C rx = rn_fma(C(-3), dm, rn_mul(C(4), b1)) + b9;
+    const C ry = rn_fma(C(-3), dp, rn_mul(C(4), b2)) + b10;
     const C rho = C(1) + drho;
     const C inv_rho = recip_uu(rho);
     C Fx = C(0), Fy = C(0), jxh = jx, jyh = jy;
     if (Force) {
         const C w = rho - k.rho_ref;
-        Fx = w * k.gx;
-        Fy = w * k.gy;
-        jxh = jx + C(0.5) * Fx;
-        jyh = jy + C(0.5) * Fy;
+        Fx = rn_mul(w, k.gx);
+        Fy = rn_mul(w, k.gy);
+        jxh = rn_fma(C(0.5), Fx, jx);
+        jyh = rn_fma(C(0.5), Fy, jy);
     }
-    const C Q1 = k.Qh + k.h1 * drho + k.k1 * dE;
-    const C R1 = k.Rh + k.h2 * drho + k.k2 * dE;
+    const C Q1 = rn_fma(k.k1, dE, rn_fma(k.h1, drho, k.Qh));
+    const C R1 = rn_fma(k.k2, dE, rn_fma(k.h2, drho, k.Rh));
     // scalar block: eps and varpi relax toward c rho + c' E (linear in the shells)
-    C i0 = k.B[0][0] * f[0] + k.B[0][1] * S1 + k.B[0][2] * S5 + k.B[0][3] * S9;
-    C i1 = k.B[1][0] * f[0] + k.B[1][1] * S1 + k.B[1][2] * S5 + k.B[1][3] * S9;
-    C i5 = k.B[2][0] * f[0] + k.B[2][1] * S1 + k.B[2][2] * S5 + k.B[2][3] * S9;
-    C i9 = k.B[3][0] * f[0] + k.B[3][1] * S1 + k.B[3][2] * S5 + k.B[3][3] * S9;
+    C i0 = rn_fma(k.B[0][3], S9, rn_fma(k.B[0][2], S5, rn_fma(k.B[0][1], S1, rn_mul(k.B[0][0], f[0]))));
+    C i1 = rn_fma(k.B[1][3], S9, rn_fma(k.B[1][2], S5, rn_fma(k.B[1][1], S1, rn_mul(k.B[1][0], f[0]))));
+    C i5 = rn_fma(k.B[2][3], S9, rn_fma(k.B[2][2], S5, rn_fma(k.B[2][1], S1, rn_mul(k.B[2][0], f[0]))));
+    C i9 = rn_fma(k.B[3][3], S9, rn_fma(k.B[3][2], S5, rn_fma(k.B[3][1], S1, rn_mul(k.B[3][0], f[0]))));
     C djx = C(0), djy = C(0);
     if (Force) {
         // j* = j + F and E* = E + 13 (|j + F|^2 - |j|^2) / rho
-        const C dEF = C(13.0 / 4004.0) * ((C(2) * jx + Fx) * Fx + (C(2) * jy + Fy) * Fy) * inv_rho;
-        i0 += C(-28) * dEF + k.src[0];
-        i1 += C(-15) * dEF + k.src[1];
-        i5 += C(-2) * dEF + k.src[2];
-        i9 += C(24) * dEF + k.src[3];
-        djx = Fx * C(1.0 / 14.0);
-        djy = Fy * C(1.0 / 14.0);
+        const C tx = rn_fma(C(2), jx, Fx), ty = rn_fma(C(2), jy, Fy);
+        const C dEF = rn_mul(rn_mul(C(13.0 / 4004.0), rn_fma(tx, Fx, rn_mul(ty, Fy))), inv_rho);
+        i0 = i0 + rn_fma(C(-28), dEF, k.src[0]);
+        i1 = i1 + rn_fma(C(-15), dEF, k.src[1]);
+        i5 = i5 + rn_fma(C(-2), dEF, k.src[2]);
+        i9 = i9 + rn_fma(C(24), dEF, k.src[3]);
+        djx = rn_mul(Fx, C(1.0 / 14.0));
+        djy = rn_mul(Fy, C(1.0 / 14.0));
     }
     // odd block: q and r relax toward j (c + h rho + k E), at j + F/2
-    const C dqx = k.l_q * (jxh * Q1 - qx), dqy = k.l_q * (jyh * Q1 - qy);
-    const C drx = k.l_r * (jxh * R1 - rx), dry = k.l_r * (jyh * R1 - ry);
+    const C dqx = rn_mul(k.l_q, rn_fma(jxh, Q1, -qx)), dqy = rn_mul(k.l_q, rn_fma(jyh, Q1, -qy));
+    const C drx = rn_mul(k.l_r, rn_fma(jxh, R1, -rx)), dry = rn_mul(k.l_r, rn_fma(jyh, R1, -ry));
     // tensor block: XX, XY toward the momentum flux, XXe toward 0
-    const C XXeq = (jxh * jxh - jyh * jyh) * inv_rho;
-    const C XXl = k.l_XX * XXeq;
-    const C t1 = XXl + k.t1X1 * X1 + k.t1X9 * X9;
-    const C t9 = C(4) * XXl + k.t9X1 * X1 + k.t9X9 * X9;
-    const C dXY = k.l_XY * (jxh * jyh * inv_rho - X5);
+    const C XXeq = rn_mul(rn_fma(jxh, jxh, -rn_mul(jyh, jyh)), inv_rho);
+    const C XXl = rn_mul(k.l_XX, XXeq);
+    const C t1 = rn_fma(k.t1X9, X9, rn_fma(k.t1X1, X1, XXl));
+    const C t9 = rn_fma(k.t9X9, X9, rn_fma(k.t9X1, X1, rn_mul(C(4), XXl)));
+    const C dXY = rn_mul(k.l_XY, rn_fma(rn_mul(jxh, jyh), inv_rho, -X5));
     // back to populations through the pairs
-    const C o1 = djx + C(-2) * dqx + C(4) * drx;
-    const C o2 = djy + C(-2) * dqy + C(4) * dry;
+    const C o1 = rn_fma(C(4), drx, rn_fma(C(-2), dqx, djx));
+    const C o2 = rn_fma(C(4), dry, rn_fma(C(-2), dqy, djy));
     const C sj = djx + djy, dj = djy - djx;
     const C sq = dqx + dqy, dq = dqx - dqy;
     const C sr = drx + dry, dr = drx - dry;
-    const C o5 = sj - sq + C(-3) * sr;
-    const C o6 = dj + dq + C(3) * dr;
-    const C o9 = C(2) * (djx + dqx) + drx;
-    const C o10 = C(2) * (djy + dqy) + dry;
+    const C o5 = rn_fma(C(-3), sr, sj - sq);
+    const C o6 = rn_fma(C(3), dr, dj + dq);
+    const C o9 = rn_fma(C(2), djx + dqx, drx);
+    const C o10 = rn_fma(C(2), djy + dqy, dry);
     const C e13 = i1 + t1, e24 = i1 - t1;
     const C e57 = i5 + dXY, e68 = i5 - dXY;
     const C e911 = i9 + t9, e1012 = i9 - t9;

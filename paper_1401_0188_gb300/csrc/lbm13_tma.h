@@ -21,25 +21,31 @@ constexpr int kTmaStage = Q * kTmaY * kTmaX;              // floats per slab
 constexpr unsigned kTmaBytes = unsigned(kTmaStage) * 4u;   // bytes per slab
 constexpr int kTmaSmem = kTmaStage * 4;                    // one slab per block
 
-// Ring-staged tiles (batch_ring_kernel): a block steps a strip of 64 columns
-// over `groups` 4-row output groups.  One producer warp streams the strip's
-// input rows in 4-row chunks -- a box of 72 x 4 x 13 floats, starting 4
-// columns left of the strip so that its first column is 16-byte aligned --
-// through a ring of kRingSlots shared-memory slots; output group g reads
-// chunks g, g + 1 and g + 2 (rows -2 .. +5 around it), so every input row is
-// loaded once per strip.  Eight consumer warps (two column halves x four rows)
-// each step one row of 32 nodes per group.  Full and empty mbarriers per slot
-// hand the chunks over; no block-wide barrier after the set-up.
+// Ring-staged tiles (batch_ring_kernel): a block of eight warps steps a
+// strip of 64 columns over `groups` 4-row output groups.  The strip's input
+// rows stream in 4-row chunks through a ring of kRingRowsTotal rows of shared
+// memory, laid out [ring row][plane][72 columns]: chunk k holds input rows
+// yb - 2 + 4k .. yb + 1 + 4k (columns x0 - 4 .. x0 + 67, so that its first
+// column is 16-byte aligned) in ring rows 4 (k mod kRingSlots) .. + 3, loaded
+// by one tensor copy whose map orders the lattice as (x, plane, y).  Output
+// group g (rows yb + 4g .. + 3) reads chunks g and g + 1 only, so with four
+// slots two chunks are in flight while two are read.  Each warp (two column
+// halves x four rows) steps one row of 32 nodes per group.  Full and empty
+// mbarriers per slot hand the chunks over; no block-wide barrier after the
+// set-up.  Two blocks per SM (16 warps).
 constexpr int kRingW = 64;
 constexpr int kRingX = kRingW + 8;
 constexpr int kRingRows = 4;
-constexpr int kRingSlots = 6;
-constexpr int kRingChunk = Q * kRingRows * kRingX;        // floats per chunk
+constexpr int kRingSlots = 4;
+constexpr int kRingRowsTotal = kRingRows * kRingSlots;     // 16: ring row = relative row & 15
+constexpr int kRingRowFloats = Q * kRingX;                 // one ring row, all planes
+constexpr int kRingChunk = kRingRows * kRingRowFloats;     // floats per chunk
 constexpr unsigned kRingBytes = unsigned(kRingChunk) * 4u;  // bytes per chunk (14,976)
 constexpr int kRingConsumers = 8;
-constexpr int kRingThreads = 32 * (kRingConsumers + 1);
-// ring slots, then one 13-float row per consumer thread for the edge gathers
-constexpr int kRingSmem = kRingSlots * int(kRingBytes) + 32 * kRingConsumers * Q * 4;
+constexpr int kRingThreads = 32 * kRingConsumers;
+static_assert((kRingRowsTotal & (kRingRowsTotal - 1)) == 0, "ring rows must be a power of two");
+// ring slots, then one 13-float row per thread for the edge gathers
+constexpr int kRingSmem = kRingSlots * int(kRingBytes) + kRingThreads * Q * 4;
 
 // One lattice's tensor maps: map[p] describes the buffer read when the step's
 // parity is p, as a 3-D tensor (x: nx, y: ny, plane: 13) with row stride
@@ -67,8 +73,8 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
 // Ring-staged batched step (FP32): one block per work item (lattice, strip of
 // 64 columns x groups 4-row groups), packed as (segment << 16) | strip.  Every
 // mbarrier wait is bounded by wait_ns of the global timer; after a timeout the
-// warp sets *err and leaves, and the producer waits (bounded) for the copies it
-// issued before it leaves.  issue = 0 withholds the copies (self-check of the
+// warp sets *err and leaves, and the producer lane waits (bounded) for the
+// copies it issued before it leaves.  issue = 0 withholds the copies (self-check of the
 // bounded waits; nothing is written then).
 cudaError_t launch_batch_ring(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
                               int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue = 1,

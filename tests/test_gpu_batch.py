@@ -83,18 +83,61 @@ def test_every_configuration_is_bit_identical(L, precision):
                     plan.step(3)
                     for g in b:
                         g.step(3)
+    if precision == 1:
+        # ring-staged strips: segments of 1 to 64 four-row groups (one group,
+        # shorter and longer than the six-slot ring, and a whole lattice)
+        for order in (0, 1, 2):
+            for groups in (1, 2, 5, 6, 7, 16, 64):
+                plan.set_config(0, 8, 0, order, groups)
+                plan.step(3)
+                for g in b:
+                    g.step(3)
+    else:
+        with pytest.raises(L.Lbm13Error):
+            plan.set_config(0, 8, 0, 0, 16)
     _same(a, b)
     plan.close()
 
 
-def test_staged_tile_wait_is_bounded(L):
-    """The staged (tensor-copy) tiles wait on an mbarrier with a time limit:
-    with the copies withheld every wait runs out, the error word is set and
-    read back, and nothing is written; with the copies issued no wait runs
-    out; the plan then steps on, bit-identical to lattices stepped alone."""
+def test_ring_strips_on_large_and_periodic_lattices(L):
+    """The ring-staged strips over lattices wider and taller than one strip
+    segment (interior nodes from the staged chunks, edges from global loads),
+    with walls, a body force and periodic sides, through 32-step graphs."""
+    specs = []
+    for i, (nx, ny, kind) in enumerate([(300, 260, "cavity"), (257, 131, "periodic"), (128, 640, "couette"),
+                                        (64, 64, "cavity"), (520, 96, "poiseuille"), (70, 400, "periodic")]):
+        p = product_pstar(0.05, 0.71)
+        T0 = (p["E0"] + 28) / 26
+        bnd = {"cavity": W.cavity(T0, 0.01, 1e-4), "couette": W.couette(T0, 0.02, 0.01),
+               "poiseuille": W.poiseuille(1e-5), "periodic": W.boundary(gx=1e-5, gy=-2e-5)}[kind]
+        specs.append((nx, ny, p, bnd, W.random_fields(nx, ny, T0, seed=300 + i, du=0.01, drho=0.005, dT=0.003)))
+    a, b = [], []
+    for i, (nx, ny, p, bnd, fields) in enumerate(specs):
+        for group in (a, b):
+            g = L.Lattice(nx, ny, p, bnd, precision=1)
+            g.set_state(*fields)
+            g.step(i % 2)
+            group.append(g)
+    plan = L.Plan(a)
+    for groups in (3, 16, 32):
+        plan.set_config(0, 8, 0, 2, groups)
+        plan.step(35)
+        for g in b:
+            g.step(35)
+        _same(a, b)
+    plan.close()
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 1), (0, 8, 16)])
+def test_staged_tile_wait_is_bounded(L, shape):
+    """The staged (tensor-copy) tiles -- slabs and ring-staged strips -- wait on
+    mbarriers with a time limit: with the copies withheld every wait runs out,
+    the error word is set and read back, and nothing is written; with the
+    copies issued no wait runs out; the plan then steps on, bit-identical to
+    lattices stepped alone."""
     a, b = _twins(L, 1)
     plan = L.Plan(a)
-    plan.set_config(4, 4, 0, 2, 1)
+    plan.set_config(shape[0], shape[1], 0, 2, shape[2])
     before = [g.save() for g in a]
     assert plan.tma_check(0.02, withhold=True) is True
     assert [g.save() for g in a] == before
@@ -112,7 +155,7 @@ def test_tune_then_step(L):
     t0 = a[0].t
     best = plan.tune(2)
     c = plan.config()
-    assert best > 0 and c["tried"] == 180
+    assert best > 0 and c["tried"] == 192  # 180 register/slab tiles + 12 ring-staged strips
     taken = a[0].t - t0
     assert taken == c["tried"] * 3
     plan.step(40)
