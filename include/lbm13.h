@@ -336,12 +336,33 @@ const char *lbm13_plan_last_error(lbm13_plan_t p);
 /* Advance every lattice of the plan by n >= 0 steps (asynchronous). */
 int lbm13_plan_step(lbm13_plan_t p, int64_t n);
 
+/* Per-lattice admission and retirement (the paper has no counterpart: they
+ * serve a request loop that steps many solves together).  lbm13_plan_add
+ * appends lattice h (same precision and device as the plan, not already in
+ * it): the plan's stream first waits (event, no host synchronisation) for the
+ * work already issued on h's own stream -- its creation and initial state --
+ * then h's entry and tensor maps are written into a free slot of the plan's
+ * device table by stream-ordered copies (the table doubles its capacity when
+ * full, re-writing every entry once) and the work list is rebuilt.
+ * lbm13_plan_remove takes h out (the last lattice moves into its slot, so the
+ * order of the others in lbm13_plan_residual changes the same way) and makes
+ * h's own stream wait for the plan's launches issued so far; h keeps its state
+ * and step counter and may be stepped alone, added again or destroyed once its
+ * stream has reached that point.  A plan keeps at least one lattice.  Neither
+ * call synchronises the host with the device; the configuration (tile shape,
+ * order) is kept, and captured step graphs are rebuilt on the next step.
+ * LBM13_EINVAL for NULL, a mismatched or duplicate lattice (add), a lattice not
+ * in the plan or the last one (remove). */
+int lbm13_plan_add(lbm13_plan_t p, lbm13_t h);
+int lbm13_plan_remove(lbm13_plan_t p, lbm13_t h);
+
 /* Autotuner: times every candidate (rows per thread R and warps per block BY
  * of the tile, row groups per tile 1, 4 or 16, persistent CTAs per SM or one
  * CTA per tile, and the order of the tiles: by lattice, round robin, largest
- * first) over steps_per_candidate real steps each (+1 warm-up), then keeps the
- * fastest.  The steps taken count as simulation steps.  *best_ms_per_step (may
- * be NULL) gets the best time. */
+ * first: 180 candidates; FP32 plans also the ring-staged strips with 8, 16, 32
+ * or 64 groups in the three orders: 12 more) over steps_per_candidate real
+ * steps each (+1 warm-up), then keeps the fastest.  The steps taken count as
+ * simulation steps.  *best_ms_per_step (may be NULL) gets the best time. */
 int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step);
 
 /* Choose a configuration: (R, BY) in {(1,4), (2,4), (4,4), (2,2), (1,8)},
@@ -349,11 +370,16 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
  * 2 largest first, groups 1 .. 64 row groups of BY * R rows per tile (a tile
  * is 32 columns x groups * BY * R rows).  LBM13_EINVAL outside these.  In an
  * FP32 plan, (4,4) with one CTA per tile stages each tile's populations
- * through shared memory by tensor copies (TMA), 8 rows at a time. */
+ * through shared memory by tensor copies (TMA), 8 rows at a time; and
+ * (R, BY) = (0, 8) (FP32 only; ctas_per_sm ignored) selects the ring-staged
+ * strips: one CTA of eight warps per strip of 64 columns x groups 4-row groups,
+ * whose input rows stream through a four-slot shared-memory ring by tensor
+ * copies while the lattice's collision coefficients stay in registers. */
 int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
 /* Self-check of the staged tiles' bounded wait (FP32 plan set to R = 4,
- * BY = 4, one CTA per tile, else LBM13_EINVAL): one staged launch with every
+ * BY = 4, one CTA per tile, or to the ring-staged strips R = 0, BY = 8; else
+ * LBM13_EINVAL): one staged launch with every
  * wait limited to timeout_s (1e-3 .. 2 s) and, when withhold != 0, no tensor
  * copy issued, so that every wait runs out and each block reports and leaves
  * without writing.  *timed_out = 1 when the error word was set (it is cleared

@@ -994,7 +994,10 @@ struct lbm13_plan {
     void *work = nullptr;
     size_t work_bytes = 0;
     int ntiles = 0;
-    double *res_dev = nullptr;  // [count][16] results of lbm13_plan_residual
+    double *res_dev = nullptr;  // [res_cap][16] results of lbm13_plan_residual
+    size_t res_cap = 0;
+    size_t cap = 0;             // lattices the device table (and maps) can hold
+    cudaEvent_t order_ev = nullptr;  // orders a lattice's own stream against the plan's
     long long nodes = 0;
     std::vector<int> cur0;
     int parity = 0;  // parity of the next launch relative to cur0
@@ -1117,10 +1120,11 @@ int plan_upload_maps(lbm13_plan_t p)
                            encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring[1]);
     }
     const size_t bytes = host.size() * sizeof(LatticeMaps);
+    const size_t cap_bytes = std::max(p->cap, host.size()) * sizeof(LatticeMaps);
     if (!p->maps || p->maps_bytes < bytes) {
         plan_free(p, p->maps);
-        p->maps = plan_alloc(p, bytes);
-        p->maps_bytes = bytes;
+        p->maps = plan_alloc(p, cap_bytes);
+        p->maps_bytes = cap_bytes;
         if (!p->maps) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan's tensor maps");
     }
     if (!p->tma_err) {
@@ -1129,12 +1133,42 @@ int plan_upload_maps(lbm13_plan_t p)
         cudaError_t e = cudaMemsetAsync(p->tma_err, 0, sizeof(unsigned), p->stream);
         if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan error word: ") + cudaGetErrorString(e));
     }
+    // pageable source: staged before the call returns, ordered on the plan's stream
     cudaError_t e = cudaMemcpyAsync(p->maps, host.data(), bytes, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("tensor map upload: ") + cudaGetErrorString(e));
     return LBM13_OK;
 }
 
+// Tensor maps of lattice i alone, into its slot (FP32 plans).
+int plan_upload_map_one(lbm13_plan_t p, size_t i)
+{
+    lbm13_t h = p->lats[i];
+    LatticeMaps m;
+    std::memset(&m, 0, sizeof m);
+    const int cur = p->cur0[i];
+    m.use = h->nx >= 64 && h->ny >= kTmaY && encode_lattice_map(h, h->buf[cur], &m.map[0]) &&
+            encode_lattice_map(h, h->buf[cur ^ 1], &m.map[1]);
+    m.ring_use = h->nx >= kRingW && h->ny >= kRingRows && encode_ring_map(h, h->buf[cur], &m.ring[0]) &&
+                 encode_ring_map(h, h->buf[cur ^ 1], &m.ring[1]);
+    cudaError_t e = cudaMemcpyAsync(static_cast<LatticeMaps *>(p->maps) + i, &m, sizeof m, cudaMemcpyHostToDevice,
+                                    p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("tensor map upload: ") + cudaGetErrorString(e));
+    return LBM13_OK;
+}
+
+template <typename T, typename C>
+BatchDesc<T, C> batch_desc(lbm13_t h, int cur)
+{
+    BatchDesc<T, C> d;
+    d.a[0] = step_args<T, C>(h, cur, coef_of<C>(h), walls_of<C>(h));
+    d.a[1] = step_args<T, C>(h, cur ^ 1, coef_of<C>(h), walls_of<C>(h));
+    d.force = h->force ? 1 : 0;
+    d.tiles_x = (h->nx + 31) / 32;
+    return d;
+}
+
+// The whole table (and, FP32, the tensor maps), every lattice taken at its
+// current buffer: the plan's parity restarts at 0.
 template <typename T, typename C>
 int plan_upload_descs(lbm13_plan_t p)
 {
@@ -1142,21 +1176,20 @@ int plan_upload_descs(lbm13_plan_t p)
     p->cur0.resize(p->lats.size());
     for (size_t i = 0; i < p->lats.size(); ++i) {
         lbm13_t h = p->lats[i];
-        host[i].a[0] = step_args<T, C>(h, h->cur, coef_of<C>(h), walls_of<C>(h));
-        host[i].a[1] = step_args<T, C>(h, h->cur ^ 1, coef_of<C>(h), walls_of<C>(h));
-        host[i].force = h->force ? 1 : 0;
-        host[i].tiles_x = (h->nx + 31) / 32;
+        host[i] = batch_desc<T, C>(h, h->cur);
         p->cur0[i] = h->cur;
     }
     const size_t bytes = host.size() * sizeof(BatchDesc<T, C>);
+    p->cap = std::max(p->cap, host.size());
+    const size_t cap_bytes = p->cap * sizeof(BatchDesc<T, C>);
     if (!p->desc || p->desc_bytes < bytes) {
         plan_free(p, p->desc);
-        p->desc = plan_alloc(p, bytes);
-        p->desc_bytes = bytes;
+        p->desc = plan_alloc(p, cap_bytes);
+        p->desc_bytes = cap_bytes;
         if (!p->desc) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan table");
     }
+    // pageable source: staged before the call returns, ordered on the plan's stream
     cudaError_t e = cudaMemcpyAsync(p->desc, host.data(), bytes, cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
     if (sizeof(T) == 4) {
         const int rc = plan_upload_maps(p);
@@ -1205,13 +1238,14 @@ int plan_build_work(lbm13_plan_t p)
     p->ntiles = int(work.size());
     const size_t bytes = std::max<size_t>(work.size(), 1) * sizeof(int2);
     if (!p->work || p->work_bytes < bytes) {
+        // the old list may still be read by launches in flight on the plan's
+        // stream: the allocator's free is stream-ordered (cudaFree waits)
         plan_free(p, p->work);
-        p->work = plan_alloc(p, bytes);
-        p->work_bytes = bytes;
+        p->work = plan_alloc(p, bytes + bytes / 2);
+        p->work_bytes = bytes + bytes / 2;
         if (!p->work) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the work list");
     }
     cudaError_t e = cudaMemcpyAsync(p->work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("work list upload: ") + cudaGetErrorString(e));
     p->grid = p->ctas <= 0 ? p->ntiles : std::min(p->ntiles, p->sms * p->ctas);
     if (p->grid < 1) p->grid = 1;
@@ -1293,6 +1327,68 @@ int plan_steps(lbm13_plan_t p, long long n)
     return LBM13_OK;
 }
 
+// Make the plan's stream wait for the work already issued on `from`.
+int plan_order_after(lbm13_plan_t p, cudaStream_t from, cudaStream_t to)
+{
+    cudaError_t e = cudaSuccess;
+    if (!p->order_ev) e = cudaEventCreateWithFlags(&p->order_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(p->order_ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, p->order_ev, 0);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("stream ordering: ") + cudaGetErrorString(e));
+    return LBM13_OK;
+}
+
+template <typename T, typename C>
+int plan_add_one(lbm13_plan_t p, lbm13_t h)
+{
+    const size_t i = p->lats.size();
+    p->lats.push_back(h);
+    // the plan's next launch reads buffer cur0 ^ parity of every lattice
+    p->cur0.push_back(h->cur ^ p->parity);
+    p->nodes += (long long)h->nx * h->ny;
+    if (i >= p->cap) {
+        // grow the table (and maps) to twice the lattices: re-upload every
+        // lattice's entry at its current buffer (plan parity restarts at 0)
+        p->cap = std::max<size_t>(2 * (i + 1), 8);
+        plan_free(p, p->desc);
+        p->desc = nullptr;
+        p->desc_bytes = 0;
+        plan_free(p, p->maps);
+        p->maps = nullptr;
+        p->maps_bytes = 0;
+        return plan_upload_descs<T, C>(p);
+    }
+    const BatchDesc<T, C> d = batch_desc<T, C>(h, p->cur0[i]);
+    cudaError_t e = cudaMemcpyAsync(static_cast<BatchDesc<T, C> *>(p->desc) + i, &d, sizeof d,
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan table entry: ") + cudaGetErrorString(e));
+    if (sizeof(T) == 4 && p->maps) return plan_upload_map_one(p, i);
+    return LBM13_OK;
+}
+
+// Lattice i leaves: the last lattice takes its slot (entry and maps copied on
+// the plan's stream, after the launches that still read them).
+template <typename T, typename C>
+int plan_remove_one(lbm13_plan_t p, size_t i)
+{
+    const size_t last = p->lats.size() - 1;
+    p->nodes -= (long long)p->lats[i]->nx * p->lats[i]->ny;
+    if (i != last) {
+        p->lats[i] = p->lats[last];
+        p->cur0[i] = p->cur0[last];
+        auto *d = static_cast<BatchDesc<T, C> *>(p->desc);
+        cudaError_t e = cudaMemcpyAsync(d + i, d + last, sizeof(BatchDesc<T, C>), cudaMemcpyDeviceToDevice, p->stream);
+        if (e == cudaSuccess && sizeof(T) == 4 && p->maps) {
+            auto *m = static_cast<LatticeMaps *>(p->maps);
+            e = cudaMemcpyAsync(m + i, m + last, sizeof(LatticeMaps), cudaMemcpyDeviceToDevice, p->stream);
+        }
+        if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("plan table move: ") + cudaGetErrorString(e));
+    }
+    p->lats.pop_back();
+    p->cur0.pop_back();
+    return LBM13_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -1349,7 +1445,41 @@ void lbm13_plan_destroy(lbm13_plan_t p)
     plan_free(p, p->maps);
     plan_free(p, p->tma_err);
     plan_free(p, p->res_dev);
+    if (p->order_ev) cudaEventDestroy(p->order_ev);
     delete p;
+}
+
+int lbm13_plan_add(lbm13_plan_t p, lbm13_t h)
+{
+    Range range_("lbm13_plan_add");
+    if (!p || !h) return pfail(p, LBM13_EINVAL, "NULL plan or lattice");
+    if (h->precision != p->precision || h->device != p->device)
+        return pfail(p, LBM13_EINVAL, "the lattice's precision or device differs from the plan's");
+    for (lbm13_t q : p->lats)
+        if (q == h) return pfail(p, LBM13_EINVAL, "the lattice is already in the plan");
+    DeviceGuard g(p->device);
+    // work issued on the lattice's own stream (creation, initial state) comes first
+    int rc = plan_order_after(p, h->stream, p->stream);
+    if (rc == LBM13_OK)
+        rc = p->precision == LBM13_FP64 ? plan_add_one<double, double>(p, h) : plan_add_one<float, float>(p, h);
+    if (rc == LBM13_OK) rc = plan_build_work(p);
+    return rc;
+}
+
+int lbm13_plan_remove(lbm13_plan_t p, lbm13_t h)
+{
+    Range range_("lbm13_plan_remove");
+    if (!p || !h) return pfail(p, LBM13_EINVAL, "NULL plan or lattice");
+    size_t i = 0;
+    while (i < p->lats.size() && p->lats[i] != h) ++i;
+    if (i == p->lats.size()) return pfail(p, LBM13_EINVAL, "the lattice is not in the plan");
+    if (p->lats.size() == 1) return pfail(p, LBM13_EINVAL, "a plan keeps at least one lattice (destroy it instead)");
+    DeviceGuard g(p->device);
+    int rc = p->precision == LBM13_FP64 ? plan_remove_one<double, double>(p, i) : plan_remove_one<float, float>(p, i);
+    // the lattice's own stream waits for the plan's launches that step it
+    if (rc == LBM13_OK) rc = plan_order_after(p, p->stream, h->stream);
+    if (rc == LBM13_OK) rc = plan_build_work(p);
+    return rc;
 }
 
 const char *lbm13_plan_last_error(lbm13_plan_t p) { return p ? p->err.c_str() : g_err.c_str(); }
@@ -1429,8 +1559,10 @@ int lbm13_plan_residual(lbm13_plan_t p, double *out)
     if (!p || !out) return pfail(p, LBM13_EINVAL, "NULL argument");
     DeviceGuard g(p->device);
     const size_t bytes = p->lats.size() * 16 * sizeof(double);
-    if (!p->res_dev) {
-        p->res_dev = static_cast<double *>(plan_alloc(p, bytes));
+    if (!p->res_dev || p->res_cap < p->lats.size()) {
+        plan_free(p, p->res_dev);
+        p->res_cap = std::max(p->cap, p->lats.size());
+        p->res_dev = static_cast<double *>(plan_alloc(p, p->res_cap * 16 * sizeof(double)));
         if (!p->res_dev) return pfail(p, LBM13_ENOMEM, "allocator returned NULL for the plan's residual buffer");
     }
     for (size_t i = 0; i < p->lats.size(); ++i) {

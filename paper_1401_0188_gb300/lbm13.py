@@ -38,7 +38,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
            "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
-           "lbm13_plan_tma_check", "lbm13_fp64_fma_rate")
+           "lbm13_plan_tma_check", "lbm13_fp64_fma_rate", "lbm13_plan_add", "lbm13_plan_remove")
 
 
 class Lbm13Error(RuntimeError):
@@ -123,6 +123,8 @@ def lib():
         "lbm13_plan_destroy": (None, [vp]),
         "lbm13_plan_last_error": (C.c_char_p, [vp]),
         "lbm13_plan_step": (C.c_int, [vp, i64]),
+        "lbm13_plan_add": (C.c_int, [vp, vp]),
+        "lbm13_plan_remove": (C.c_int, [vp, vp]),
         "lbm13_plan_tune": (C.c_int, [vp, C.c_int, dp]),
         "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
         "lbm13_plan_config": (C.c_int, [vp, C.POINTER(i64)]),
@@ -436,6 +438,18 @@ class Plan:
 
     def step(self, n=1):
         _pcheck(lib().lbm13_plan_step(self._h, int(n)), self._h)
+
+    def add(self, lattice):
+        """Admit one more lattice (ordered after the work on its own stream)."""
+        _pcheck(lib().lbm13_plan_add(self._h, lattice.handle), self._h)
+        self.lattices.append(lattice)
+
+    def remove(self, lattice):
+        """Retire a lattice: the last one takes its row in residual()."""
+        _pcheck(lib().lbm13_plan_remove(self._h, lattice.handle), self._h)
+        i = next(k for k, l in enumerate(self.lattices) if l is lattice)
+        self.lattices[i] = self.lattices[-1]
+        self.lattices.pop()
 
     def tune(self, steps_per_candidate=4):
         best = C.c_double()

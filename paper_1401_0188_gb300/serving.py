@@ -3,13 +3,18 @@
 Requests arrive over time (a seeded Poisson stream).  A request is admitted
 when a slot is free and its lattice fits in the device-memory budget; from then
 on its populations stay on the device and it is stepped together with every
-other admitted request in one batched launch per time step (a plan over the
-active lattices, rebuilt when the set changes).  Every `check_every` steps the
-FP64 residuals of all active lattices are read back in one synchronisation;
-a request retires when its residual reaches its tolerance, freeing its slot and
-memory for the queue.  Admission and retirement happen only between rounds of
-`check_every` steps, so each request sees the same sequence of steps and checks
-whether it runs alone or in a mix: its result does not depend on the mix.
+other admitted request in one batched launch per time step (one plan over the
+active lattices).  Rounds of `check_every` steps are launched asynchronously;
+while a round runs on the GPU, requests that arrive are admitted on the host
+and their lattices created and initialised on a second CUDA stream, so that
+their set-up overlaps the round.  At the end of the round the FP64 residuals
+of all active lattices are read back in one synchronisation; a request retires
+when its residual reaches its tolerance (lbm13_plan_remove, freeing its slot
+and memory for the queue) and the newly admitted lattices join the plan
+(lbm13_plan_add) for the next round.  Admission and retirement take effect
+only between rounds, so each request sees the same sequence of steps and
+checks whether it runs alone or in a mix: its result does not depend on the
+mix.
 
 The baseline mode steps each lattice with its own launches in FP64 (the plain
 one-lattice-per-launch path), with the same admission and checks.
@@ -83,18 +88,23 @@ def lattice_bytes(nx, ny, precision):
     return 2 * 13 * elem * pitch * ny + 8 * (6 * nx * ny + 1216 * 16 + 32)
 
 
-def poisson_trace(n, rate, seed=5151, side_range=(64, 192), ra_range=(1e3, 1e5), Pr=0.71, tol=1e-7):
+def poisson_trace(n, rate, seed=5151, side_range=(64, 192), ra_range=(1e3, 1e5), Pr=0.71, tol=1e-7,
+                  pr_range=None):
     """n requests, exponential inter-arrival times of mean 1/rate, alternating
     cavity/channel (50/50), side log-uniform in side_range rounded to a
-    multiple of 32, Ra log-uniform in ra_range."""
+    multiple of 32, Ra log-uniform in ra_range; Pr fixed, or uniform in
+    pr_range when given.  Each request draws its values in turn, so the first
+    k requests of a longer trace are the trace of k requests."""
     g = np.random.Generator(np.random.PCG64(seed))
-    t = np.cumsum(g.exponential(1.0 / rate, n))
     out = []
+    t = 0.0
     for i in range(n):
+        t += float(g.exponential(1.0 / rate))
         side = int(round(math.exp(g.uniform(math.log(side_range[0]), math.log(side_range[1]))) / 32) * 32)
         ra = math.exp(g.uniform(math.log(ra_range[0]), math.log(ra_range[1])))
+        pr = float(g.uniform(*pr_range)) if pr_range is not None else Pr
         kind = "cavity" if i % 2 == 0 else "channel"
-        out.append(Request(i, kind, max(32, side), ra, Pr, tol, float(t[i])))
+        out.append(Request(i, kind, max(32, side), ra, pr, tol, t))
     return out
 
 
@@ -111,10 +121,13 @@ class _Active:
 
 class Server:
     """`backend` provides Lattice and Plan (the CUDA binding by default; the
-    CPU tests of the admission logic pass a stand-in)."""
+    CPU tests of the admission logic pass a stand-in).  With `overlap` (and
+    the CUDA backend), new lattices are set up on a second stream while the
+    current round runs."""
 
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
-                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config=(1, 4, 0, 2, 1)):
+                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config=(1, 4, 0, 2, 1),
+                 overlap=True, poll_s=0.0005):
         # plan_config: (R, BY, ctas_per_sm, order, groups) of the batched step
         self.plan_config = tuple(plan_config)
         self.backend = backend
@@ -125,55 +138,62 @@ class Server:
         self.max_steps = max_steps
         self.batched = batched
         self.realtime = realtime
+        self.overlap = overlap
+        self.poll_s = poll_s
 
     def run(self, requests):
         pending = sorted(requests, key=lambda r: r.arrival)
         active, results = [], []
-        used = 0
+        self._used = 0
         plan = None
         t0 = time.perf_counter()
-        clock_offset = 0.0
-        now = lambda: time.perf_counter() - t0 + clock_offset
+        self._clock_offset = 0.0
+        now = lambda: time.perf_counter() - t0 + self._clock_offset
+        side = None
+        if self.batched and self.overlap and self.backend is lbm13:
+            import torch
+            side = torch.cuda.Stream()
         lattice_steps = 0
-        while pending or active:
-            changed = False
-            while pending and pending[0].arrival <= now() and len(active) < self.max_slots:
-                nx, ny, p, bnd = request_setup(pending[0])
-                b = lattice_bytes(nx, ny, self.precision)
-                if used + b > self.hbm_budget:
-                    if not active:
-                        raise ValueError(f"request {pending[0].rid} needs {b} bytes, above the budget")
-                    break
-                req = pending.pop(0)
-                lat = self.backend.Lattice(nx, ny, p, bnd, precision=self.precision)
-                lat.set_state(1.0, 0.0, 0.0, P.rest_temperature(p))
-                lat.residual()
-                active.append(_Active(req, lat, nx, ny, b, now()))
-                used += b
-                changed = True
+        joining = []     # admitted during the current round: join the next one
+        while pending or active or joining:
+            # newly admitted lattices join the plan for this round
+            for a in joining:
+                if self.batched and plan is not None:
+                    plan.add(a.lat)
+                active.append(a)
+            if self.batched and joining and plan is None:
+                plan = self.backend.Plan([a.lat for a in active])
+                plan.set_config(*self.plan_config)
+            joining = []
             if not active:
-                wait = pending[0].arrival - now()
-                if wait > 0:
-                    if self.realtime:
-                        time.sleep(wait)
-                    else:
-                        clock_offset += wait
+                joining = self._admit(pending, active, joining, now, side)
+                if not joining:
+                    wait = pending[0].arrival - now()
+                    if wait > 0:
+                        if self.realtime:
+                            time.sleep(wait)
+                        else:
+                            self._clock_offset += wait
                 continue
             if self.batched:
-                if changed or plan is None:
-                    if plan is not None:
-                        plan.close()
-                    plan = self.backend.Plan([a.lat for a in active])
-                    plan.set_config(*self.plan_config)
                 plan.step(self.check_every)
+                done_ev = self._record(plan)
+                # admit arrivals while the round runs (set-up on the side stream)
+                while True:
+                    joining = self._admit(pending, active, joining, now, side)
+                    if done_ev is None or not self.realtime or done_ev.query():
+                        break
+                    time.sleep(self.poll_s)
                 res = plan.residual(raise_on_divergence=False)
             else:
                 for a in active:
                     a.lat.step(self.check_every)
                 res = np.array([a.lat.residual(raise_on_divergence=False) for a in active])
+                joining = self._admit(pending, active, joining, now, side)
             lattice_steps += self.check_every * sum(a.nx * a.ny for a in active)
             keep = []
-            for a, r in zip(active, res):
+            for a, r in zip(list(plan.lattices if self.batched else [a.lat for a in active]), res):
+                a = next(x for x in active if x.lat is a)
                 a.steps += self.check_every
                 done = (r[13] > 0 and r[0] <= a.req.tol) or a.steps >= self.max_steps or r[12] > 0
                 if done:
@@ -182,14 +202,16 @@ class Server:
                                           a.admitted, t, a.steps, bool(r[13] > 0 and r[0] <= a.req.tol),
                                           float(r[0]), float(r[8]), float(r[9]), float(r[10]), float(r[11]),
                                           float(r[4]), t - a.req.arrival))
+                    if self.batched:
+                        if len(plan.lattices) > 1:
+                            plan.remove(a.lat)
+                        else:
+                            plan.close()
+                            plan = None
                     a.lat.close()
-                    used -= a.bytes
-                    changed = True
+                    self._used -= a.bytes
                 else:
                     keep.append(a)
-            if changed and plan is not None:
-                plan.close()
-                plan = None
             active = keep
         if plan is not None:
             plan.close()
@@ -199,8 +221,39 @@ class Server:
                    "wall_s": wall, "p50_tts_s": float(np.percentile(tts, 50)), "p99_tts_s": float(np.percentile(tts, 99)),
                    "throughput_req_s": len(results) / wall, "MLUPS": lattice_steps / wall / 1e6,
                    "precision": "fp64" if self.precision == lbm13.FP64 else "fp32-deviation",
-                   "batched": self.batched}
+                   "batched": self.batched, "overlap": side is not None}
         return sorted(results, key=lambda r: r.rid), summary
+
+    def _record(self, plan):
+        """An event after the round just launched (None for stand-in plans)."""
+        stream = getattr(plan, "stream", None)
+        if stream is None or self.backend is not lbm13:
+            return None
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
+    def _admit(self, pending, active, joining, now, side):
+        """Admit the requests that have arrived, as slots and the budget allow;
+        their lattices start at rest with a residual snapshot."""
+        while pending and pending[0].arrival <= now() and len(active) + len(joining) < self.max_slots:
+            nx, ny, p, bnd = request_setup(pending[0])
+            b = lattice_bytes(nx, ny, self.precision)
+            if self._used + b > self.hbm_budget:
+                if not active and not joining:
+                    raise ValueError(f"request {pending[0].rid} needs {b} bytes, above the budget")
+                break
+            req = pending.pop(0)
+            if side is not None:
+                lat = self.backend.Lattice(nx, ny, p, bnd, precision=self.precision, stream=side)
+            else:
+                lat = self.backend.Lattice(nx, ny, p, bnd, precision=self.precision)
+            lat.set_state(None, None, None, None)  # rest: rho 1, u 0, T T0
+            lat.residual()
+            joining.append(_Active(req, lat, nx, ny, b, now()))
+            self._used += b
+        return joining
 
 
 def batch_workload(n=256, seed=4242, sides=(64, 96, 128, 192, 256, 384, 512), ra_range=(1e3, 1e6),

@@ -99,6 +99,56 @@ def test_every_configuration_is_bit_identical(L, precision):
     plan.close()
 
 
+@pytest.mark.parametrize("precision,shape", [(0, (1, 4, 0, 2, 4)), (1, (1, 4, 0, 2, 4)), (1, (0, 8, 0, 2, 16))])
+def test_admit_and_retire_keep_lattices_bit_identical(L, precision, shape):
+    """lbm13_plan_add / lbm13_plan_remove: lattices join one at a time (past
+    the table's first capacity, at different buffer parities, one just
+    re-initialised on its own stream), leave from the middle, the end and the
+    front, and step alone afterwards; every lattice stays bit-identical to its
+    twin stepped alone, and residual rows follow the plan's order."""
+    import torch
+    a, b = _twins(L, precision)
+    side = torch.cuda.Stream()
+    plan = L.Plan(a[:2])
+    plan.set_config(*shape)
+    inside = [0, 1]
+    plan.step(5)
+    for k in inside:
+        b[k].step(5)
+    for k in range(2, len(a)):
+        if k == 5:
+            # set up on another stream right before joining: the plan's launches
+            # must wait for it
+            a[k].set_stream(side)
+            b[k].set_stream(side)
+            fields = _specs()[k][4]
+            a[k].set_state(*fields)
+            b[k].set_state(*fields)
+        plan.add(a[k])
+        inside.append(k)
+        plan.step(3)
+        for j in inside:
+            b[j].step(3)
+    assert [id(g) for g in plan.lattices] == [id(a[k]) for k in inside]
+    for victim in (4, len(a) - 1, 0):
+        plan.remove(a[victim])
+        inside.remove(victim)
+        plan.step(33)  # one 32-step graph and one launch
+        for j in inside:
+            b[j].step(33)
+        a[victim].step(2)  # alone again, on its own stream
+        b[victim].step(2)
+    r = plan.residual()
+    assert [int(row[14]) for row in r] == [g.t for g in plan.lattices]
+    torch.cuda.synchronize()
+    _same(a, b)
+    with pytest.raises(L.Lbm13Error):
+        plan.add(plan.lattices[0])  # already in the plan
+    with pytest.raises(L.Lbm13Error):
+        plan.remove(a[0])  # not in the plan
+    plan.close()
+
+
 def test_ring_strips_on_large_and_periodic_lattices(L):
     """The ring-staged strips over lattices wider and taller than one strip
     segment (interior nodes from the staged chunks, edges from global loads),

@@ -61,6 +61,16 @@ class FakePlan:
     def set_config(self, *a):
         pass
 
+    def add(self, lat):
+        assert all(g is not lat for g in self.lattices)
+        self.lattices.append(lat)
+
+    def remove(self, lat):
+        # the last lattice takes the removed one's row, as in lbm13_plan_remove
+        i = next(k for k, g in enumerate(self.lattices) if g is lat)
+        self.lattices[i] = self.lattices[-1]
+        self.lattices.pop()
+
     def step(self, n):
         for g in self.lattices:
             g.step(n)
