@@ -75,8 +75,14 @@ typedef struct {
 typedef enum {
     LBM13_PERIODIC = 0,   /* opposite sides must both be periodic */
     LBM13_WALL_BB = 1,    /* adiabatic no-slip wall: every crossing link bounces back (Sec. 9) */
-    LBM13_WALL_MIXED = 2  /* velocity + temperature wall: links normal to the wall use
+    LBM13_WALL_MIXED = 2, /* velocity + temperature wall: links normal to the wall use
                              anti-bounce-back, diagonal links bounce-back (Sec. 7) */
+    LBM13_HALO = 3        /* south or north only: the lattice is one y-slab of a larger one, and
+                             its two rows next to this side are halo rows holding the
+                             neighbouring slab's rows (the paper's own lattice has no such
+                             side: its stencil, Sec. 2, reaches two rows, hence two halo
+                             rows).  The step never writes halo rows and pulls from them
+                             like any row; lbm13_halo_unpack fills them after each step. */
 } lbm13_wall_kind;
 
 /* A wall lies half a link outside the first/last node.  u_t is its velocity
@@ -399,6 +405,33 @@ int lbm13_plan_config(lbm13_plan_t p, int64_t out[9]);
  * LBM13_ETIMEOUT when a staged tile's tensor copy did not complete within
  * 1 s since the last call (its tile was left unstepped). */
 int lbm13_plan_residual(lbm13_plan_t p, double *out);
+
+/* y-slab halo exchange (the paper has no counterpart: it runs one lattice on
+ * one GPU; this splits a lattice into y-slabs, one per device or one per
+ * stream, that exchange two rows per side after every step).  A slab is a
+ * lattice whose south and/or north side is LBM13_HALO; with nx columns and
+ * ny rows (halo rows included) it must keep at least four rows that are not
+ * halo rows.  A packed halo is [2 rows][4 populations][nx] in the lattice's
+ * storage type (double, or float deviations f_j - w_j), *bytes of
+ * lbm13_halo_bytes.
+ *
+ * lbm13_halo_pack(h, side, out): the two rows next to the halo rows of
+ * `side` (rows 2, 3 for LBM13_HALO_SOUTH; ny-4, ny-3 for LBM13_HALO_NORTH) of
+ * the stored state, populations that move across that side (v_y < 0:
+ * 4, 7, 8, 12 at south; v_y > 0: 2, 5, 6, 10 at north), into the caller's
+ * DEVICE buffer `out`, in stream order on h's stream.
+ * lbm13_halo_unpack(h, side, in): writes a packed halo of the neighbouring
+ * slab into h's halo rows of `side` (rows 0, 1 at south, ny-2, ny-1 at
+ * north: the populations that move into h across that side), in stream order.
+ * The lower slab's north pack is the upper slab's south unpack and vice versa;
+ * the caller orders the streams of the two slabs (and moves the buffer between
+ * devices where they differ).  LBM13_EINVAL for NULL, a side that is not
+ * LBM13_HALO on h, or a lattice with fewer than four non-halo rows. */
+#define LBM13_HALO_SOUTH 2
+#define LBM13_HALO_NORTH 3
+int lbm13_halo_bytes(lbm13_t h, size_t *bytes);
+int lbm13_halo_pack(lbm13_t h, int side, void *out);
+int lbm13_halo_unpack(lbm13_t h, int side, const void *in);
 
 /* Measured FP64 instruction rate of the current device, the denominator of
  * the FP64 time step's roofline (that step is bound by its FP64 pipe, not by

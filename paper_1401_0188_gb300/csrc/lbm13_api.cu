@@ -472,8 +472,8 @@ int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
 
 int check_wall(const lbm13_wall &w)
 {
-    return (w.kind == PERIODIC || w.kind == WALL_BB || w.kind == WALL_MIXED) && std::isfinite(w.u_t) &&
-           std::isfinite(w.T);
+    return (w.kind == PERIODIC || w.kind == WALL_BB || w.kind == WALL_MIXED || w.kind == HALO) &&
+           std::isfinite(w.u_t) && std::isfinite(w.T);
 }
 
 unsigned popcount18(unsigned m)
@@ -595,10 +595,14 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
         return fail(nullptr, LBM13_EINVAL, "wall_density must be LBM13_WALL_DENSITY_EXTRAPOLATE or _ZERO_FLUX");
     if ((b.west.kind == PERIODIC) != (b.east.kind == PERIODIC) || (b.south.kind == PERIODIC) != (b.north.kind == PERIODIC))
         return fail(nullptr, LBM13_EINVAL, "opposite sides must both be periodic or both be walls");
-    const int min_x = b.west.kind == PERIODIC ? 2 : 4, min_y = b.south.kind == PERIODIC ? 2 : 4;
+    if (b.west.kind == HALO || b.east.kind == HALO)
+        return fail(nullptr, LBM13_EINVAL, "halo sides (y-slabs) are south or north only");
+    const int halos = (b.south.kind == HALO) + (b.north.kind == HALO);
+    const int min_x = b.west.kind == PERIODIC ? 2 : 4, min_y = b.south.kind == PERIODIC ? 2 : 4 + 2 * halos;
     if (nx < min_x || ny < min_y || nx > (1 << 20) || ny > 32768 || (long long)nx * ny > 0x7fffffffLL)
         return fail(nullptr, LBM13_EINVAL,
-                    "lattice size out of range (>= 2, >= 4 along a walled axis, nx <= 2^20, ny <= 32768, nx*ny < 2^31)");
+                    "lattice size out of range (>= 2, >= 4 along a walled axis plus 2 rows per halo side, nx <= 2^20, "
+                    "ny <= 32768, nx*ny < 2^31)");
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, LBM13_EINVAL, "allocator without alloc/free");
 
     lbm13_t h = new lbm13_lattice();
@@ -976,6 +980,59 @@ bool lbm13_state_view(const lbm13_lattice *h, lbm13::StateView *v)
     v->stream = h->stream;
     return true;
 }
+
+// ------------------------------------------------------------ y-slab halos
+
+namespace {
+
+int halo_check(lbm13_t h, int side, const void *buf)
+{
+    if (!h || !buf) return fail(h, LBM13_EINVAL, "NULL argument");
+    if (side != LBM13_HALO_SOUTH && side != LBM13_HALO_NORTH) return fail(h, LBM13_EINVAL, "side must be south or north");
+    const lbm13_wall &w = side == LBM13_HALO_SOUTH ? h->b.south : h->b.north;
+    if (w.kind != HALO) return fail(h, LBM13_EINVAL, "that side of the lattice is not a halo side");
+    return LBM13_OK;
+}
+
+int halo_move(lbm13_t h, int side, void *buf, bool pack)
+{
+    DeviceGuard g(h->device);
+    const int s = side == LBM13_HALO_SOUTH ? SOUTH : NORTH;
+    cudaError_t e = h->precision == LBM13_FP64
+                        ? launch_halo<double>(static_cast<double *>(h->buf[h->cur]), h->nx, h->ny, h->pitch, h->plane,
+                                              s, pack, static_cast<double *>(buf), h->stream)
+                        : launch_halo<float>(static_cast<float *>(h->buf[h->cur]), h->nx, h->ny, h->pitch, h->plane, s,
+                                             pack, static_cast<float *>(buf), h->stream);
+    if (e != cudaSuccess) return fail(h, LBM13_ECUDA, std::string("halo launch: ") + cudaGetErrorString(e));
+    return LBM13_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int lbm13_halo_bytes(lbm13_t h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(h, LBM13_EINVAL, "NULL argument");
+    *bytes = size_t(8) * size_t(h->nx) * h->elem;
+    return LBM13_OK;
+}
+
+int lbm13_halo_pack(lbm13_t h, int side, void *out)
+{
+    Range range_("lbm13_halo_pack");
+    const int rc = halo_check(h, side, out);
+    return rc != LBM13_OK ? rc : halo_move(h, side, out, true);
+}
+
+int lbm13_halo_unpack(lbm13_t h, int side, const void *in)
+{
+    Range range_("lbm13_halo_unpack");
+    const int rc = halo_check(h, side, in);
+    return rc != LBM13_OK ? rc : halo_move(h, side, const_cast<void *>(in), false);
+}
+
+} // extern "C"
 
 // ------------------------------------------------------------------ plans
 //

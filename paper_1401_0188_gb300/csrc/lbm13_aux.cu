@@ -396,6 +396,47 @@ cudaError_t launch_moments(const ReadArgs<T> &a, double *out, unsigned mask, cud
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ y-slab halos
+//
+// Entry i of a packed halo [2 rows][4 populations][nx]: pack reads the rows
+// next to the halo rows of `side` (south: 2, 3; north: ny-4, ny-3) for the
+// populations that move across it (south: v_y < 0; north: v_y > 0); unpack
+// writes the halo rows (south: 0, 1; north: ny-2, ny-1) for the populations
+// that move in (south: v_y > 0; north: v_y < 0).
+__device__ __forceinline__ int halo_plane(bool up, int k)
+{
+    return up ? (k == 0 ? 2 : k == 1 ? 5 : k == 2 ? 6 : 10) : (k == 0 ? 4 : k == 1 ? 7 : k == 2 ? 8 : 12);
+}
+
+template <typename T>
+__global__ void halo_kernel(T *__restrict__ f, int nx, int ny, long long pitch, long long plane, int side, int pack,
+                            T *__restrict__ buf)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 8LL * nx) return;
+    const int x = int(i % nx), k = int((i / nx) % 4), r = int(i / (4LL * nx));
+    const bool south = side == SOUTH;
+    const int y = pack ? (south ? 2 + r : ny - 4 + r) : (south ? r : ny - 2 + r);
+    const bool up = pack ? !south : south;
+    T *p = f + (long long)halo_plane(up, k) * plane + (long long)y * pitch + x;
+    if (pack)
+        buf[i] = *p;
+    else
+        *p = buf[i];
+}
+
+template <typename T>
+cudaError_t launch_halo(T *f, int nx, int ny, long long pitch, long long plane, int side, bool pack, T *buf,
+                        cudaStream_t s)
+{
+    const long long n = 8LL * nx;
+    halo_kernel<T><<<unsigned((n + 255) / 256), 256, 0, s>>>(f, nx, ny, pitch, plane, side, pack ? 1 : 0, buf);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_halo<double>(double *, int, int, long long, long long, int, bool, double *, cudaStream_t);
+template cudaError_t launch_halo<float>(float *, int, int, long long, long long, int, bool, float *, cudaStream_t);
+
 int reduce_blocks(int nx, int ny)
 {
     const long long n = (long long)nx * ny;

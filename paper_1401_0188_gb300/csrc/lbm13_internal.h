@@ -13,7 +13,7 @@
 namespace lbm13 {
 
 enum Side { WEST = 0, EAST = 1, SOUTH = 2, NORTH = 3 };
-enum WallKind { PERIODIC = 0, WALL_BB = 1, WALL_MIXED = 2 };
+enum WallKind { PERIODIC = 0, WALL_BB = 1, WALL_MIXED = 2, HALO = 3 };
 
 // One side of the lattice as the kernels see it.
 template <typename C>
@@ -140,6 +140,13 @@ bool batch_shape_supported(int R, int BY);
 template <typename T, typename C>
 cudaError_t launch_batch(const BatchDesc<T, C> *descs, const int2 *work, int ntiles, int parity, int R, int BY,
                          int groups, int grid, cudaStream_t s);
+
+// y-slab halo rows (HALO sides): pack the two rows next to the halo rows of
+// side `side` (SOUTH or NORTH), the four populations that cross it, into
+// out[2][4][nx]; unpack writes in[2][4][nx] into the halo rows of `side`.
+template <typename T>
+cudaError_t launch_halo(T *f, int nx, int ny, long long pitch, long long plane, int side, bool pack, T *buf,
+                        cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_init(T *f, int nx, int ny, long long pitch, long long plane, const Coef<double> &k,

@@ -294,6 +294,8 @@ __device__ __forceinline__ void process_column(const StepArgs<T, C> &a, int x, i
         for (int r = 0; r < R; ++r) {
             const int y = y0 + r;
             if (y >= ny) break;
+            // halo rows of a y-slab are written by the exchange, never stepped
+            if ((y < 2 && a.wall[SOUTH].kind == HALO) || (y >= ny - 2 && a.wall[NORTH].kind == HALO)) continue;
             C f[Q];
             gather_general(a, x, y, slot);
 #pragma unroll

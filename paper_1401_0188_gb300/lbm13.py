@@ -17,7 +17,8 @@ from . import build as _build
 Q = 13
 PARAM_FIELDS = ("E0", "c1", "k2", "c_epsE", "c_vpi_rho", "c_vpi_E", "Pr", "nu",
                 "s_eps", "s_vpi", "s_r", "s_XXe")
-PERIODIC, WALL_BB, WALL_MIXED = 0, 1, 2
+PERIODIC, WALL_BB, WALL_MIXED, HALO = 0, 1, 2, 3
+HALO_SOUTH, HALO_NORTH = 2, 3
 FP64, FP32_DEVIATION = 0, 1
 WALL_DENSITY_EXTRAPOLATE, WALL_DENSITY_ZERO_FLUX = 0, 1
 PERSISTENT_AUTO, PERSISTENT_OFF, PERSISTENT_ON = 0, 1, 2
@@ -38,7 +39,8 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_plan_last_error", "lbm13_plan_step", "lbm13_plan_tune", "lbm13_plan_set_config",
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
            "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
-           "lbm13_plan_tma_check", "lbm13_fp64_fma_rate", "lbm13_plan_add", "lbm13_plan_remove")
+           "lbm13_plan_tma_check", "lbm13_fp64_fma_rate", "lbm13_plan_add", "lbm13_plan_remove",
+           "lbm13_halo_bytes", "lbm13_halo_pack", "lbm13_halo_unpack")
 
 
 class Lbm13Error(RuntimeError):
@@ -124,6 +126,9 @@ def lib():
         "lbm13_plan_last_error": (C.c_char_p, [vp]),
         "lbm13_plan_step": (C.c_int, [vp, i64]),
         "lbm13_plan_add": (C.c_int, [vp, vp]),
+        "lbm13_halo_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "lbm13_halo_pack": (C.c_int, [vp, C.c_int, vp]),
+        "lbm13_halo_unpack": (C.c_int, [vp, C.c_int, vp]),
         "lbm13_plan_remove": (C.c_int, [vp, vp]),
         "lbm13_plan_tune": (C.c_int, [vp, C.c_int, dp]),
         "lbm13_plan_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -376,6 +381,21 @@ class Lattice:
         n = C.c_ulonglong(0)
         _check(lib().lbm13_debug_violations(self._h, C.byref(n)), self._h)
         return int(n.value)
+
+    def halo_bytes(self):
+        """Bytes of one packed halo: [2 rows][4 populations][nx] in the storage type."""
+        n = C.c_size_t()
+        _check(lib().lbm13_halo_bytes(self._h, C.byref(n)), self._h)
+        return n.value
+
+    def halo_pack(self, side, out):
+        """Pack the rows next to halo side `side` (HALO_SOUTH / HALO_NORTH) into
+        `out`, a contiguous CUDA tensor of halo_bytes() bytes (stream-ordered)."""
+        _check(lib().lbm13_halo_pack(self._h, int(side), C.c_void_p(out.data_ptr())), self._h)
+
+    def halo_unpack(self, side, buf):
+        """Write a neighbour's packed halo into the halo rows of `side`."""
+        _check(lib().lbm13_halo_unpack(self._h, int(side), C.c_void_p(buf.data_ptr())), self._h)
 
     def set_persistent(self, mode):
         """PERSISTENT_AUTO (default), PERSISTENT_OFF or PERSISTENT_ON: whether
