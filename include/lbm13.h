@@ -196,12 +196,30 @@ int lbm13_derive(const lbm13_params *params, double *out);
  * parameter set. */
 int lbm13_linear_growth(const lbm13_params *params, double ux, double uy, int n, double *growth);
 
-/* Create an nx x ny lattice (nx, ny >= 2; >= 4 along an axis that has walls;
- * nx <= 2^20, ny <= 32768, nx * ny < 2^31) on the current CUDA device.  `alloc` may be NULL (cudaMalloc),
+/* The scan of lbm13_linear_growth for `count` cases at once on the current
+ * device (the dispersion-root procedure of the end of Sec. 2, run for many
+ * candidate parameter sets and flows): case c is parameter set params[c]
+ * about u = (ux[c], uy[c]) on the n x n k-grid; growth[c] = max |z| - 1.  The
+ * collision Jacobians are assembled on the host; one GPU thread per (case, k)
+ * reduces the 13 x 13 amplification matrix to Hessenberg form and runs the
+ * shifted QR iteration (the same code as the host scan).  Host arrays of
+ * `count` entries, owned by the caller; `stream` is a cudaStream_t (NULL =
+ * legacy default) that the call synchronises; its scratch comes from the
+ * stream-ordered allocator and is released before it returns.  LBM13_EINVAL
+ * for NULL, count < 1, n outside 1..129, a rejected parameter set or an
+ * eigenvalue iteration that does not converge; LBM13_ECUDA on a CUDA error. */
+int lbm13_linear_growth_batch(const lbm13_params *params, const double *ux, const double *uy, int count, int n,
+                              double *growth, void *stream);
+
+/* Create an nx x ny lattice (nx, ny >= 2; >= 4 along an axis that has walls,
+ * plus 2 rows per halo side; nx <= 2^20, ny <= 32768, nx * ny < 2^31) on the
+ * current CUDA device.  `alloc` may be NULL (cudaMalloc),
  * `stream` is a cudaStream_t (NULL = legacy default stream).  The state starts
  * at rest: rho = 1, u = 0, T = T0.  On success *out is a new handle.
- * LBM13_EUNSTABLE when sigma_q <= 0 or when the linearised step at rest
- * amplifies a Fourier mode (lbm13_linear_growth on a 9 x 9 k-grid above 1e-9). */
+ * LBM13_EUNSTABLE when sigma_q <= 0 or when the linearised step amplifies a
+ * Fourier mode (lbm13_linear_growth on a 9 x 9 k-grid above 1e-9) at rest or,
+ * where a wall moves, in a uniform flow at the largest wall speed along x and
+ * along y. */
 int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundary *boundary,
                  int precision, const lbm13_allocator *alloc, void *stream, lbm13_t *out);
 

@@ -562,6 +562,25 @@ int lbm13_linear_growth(const lbm13_params *params, double ux, double uy, int n,
     return LBM13_OK;
 }
 
+int lbm13_linear_growth_batch(const lbm13_params *params, const double *ux, const double *uy, int count, int n,
+                              double *growth, void *stream)
+{
+    Range range_("lbm13_linear_growth_batch");
+    if (!params || !ux || !uy || !growth || count < 1 || n < 1 || n > 129)
+        return fail(nullptr, LBM13_EINVAL, "NULL argument, count < 1 or n outside 1..129");
+    std::vector<double> D(size_t(count) * LBM13_DERIVED_COUNT);
+    for (int c = 0; c < count; ++c) {
+        if (!std::isfinite(ux[c]) || !std::isfinite(uy[c]))
+            return fail(nullptr, LBM13_EINVAL, "non-finite background velocity");
+        const int st = derive(params[c], D.data() + size_t(c) * LBM13_DERIVED_COUNT);
+        if (st != LBM13_OK) return fail(nullptr, st, "a parameter set was rejected by lbm13_derive");
+    }
+    const int rc = linear_growth_batch(params, D.data(), ux, uy, count, n, growth, static_cast<cudaStream_t>(stream));
+    if (rc == LBM13_EINVAL) return fail(nullptr, rc, "eigenvalue iteration did not converge");
+    if (rc != LBM13_OK) return fail(nullptr, rc, "CUDA error in the batched stability scan");
+    return LBM13_OK;
+}
+
 const char *lbm13_last_error(lbm13_t h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 int lbm13_debug_violations(lbm13_t h, unsigned long long *count)
@@ -619,14 +638,22 @@ int lbm13_create(int nx, int ny, const lbm13_params *params, const lbm13_boundar
         return fail(nullptr, st, st == LBM13_EUNSTABLE ? "sigma_q <= 0: no positive relaxation time for q"
                                                        : "parameter out of range (rates in (0,2), nu > 0, Pr > 0)");
     }
-    // the linearised step at rest must not amplify any Fourier mode
-    double growth = 0.0;
-    if (linear_growth(h->p, h->derived, 0.0, 0.0, kCreateScanN, &growth) != LBM13_OK || !(growth <= kCreateScanTol)) {
-        delete h;
-        char msg[160];
-        std::snprintf(msg, sizeof msg, "linearly unstable at rest: max |z| - 1 = %.3g over a %d x %d k-grid",
-                      growth, kCreateScanN, kCreateScanN);
-        return fail(nullptr, LBM13_EUNSTABLE, msg);
+    // the linearised step must not amplify any Fourier mode at rest, nor in a
+    // uniform flow at the largest wall speed along either axis
+    const double uw = std::max({std::fabs(b.west.u_t), std::fabs(b.east.u_t), std::fabs(b.south.u_t),
+                                std::fabs(b.north.u_t)});
+    const double scan_u[3][2] = {{0.0, 0.0}, {uw, 0.0}, {0.0, uw}};
+    for (int k = 0; k < (uw > 0.0 ? 3 : 1); ++k) {
+        double growth = 0.0;
+        if (linear_growth(h->p, h->derived, scan_u[k][0], scan_u[k][1], kCreateScanN, &growth) != LBM13_OK ||
+            !(growth <= kCreateScanTol)) {
+            delete h;
+            char msg[200];
+            std::snprintf(msg, sizeof msg,
+                          "linearly unstable at u = (%.3g, %.3g): max |z| - 1 = %.3g over a %d x %d k-grid",
+                          scan_u[k][0], scan_u[k][1], growth, kCreateScanN, kCreateScanN);
+            return fail(nullptr, LBM13_EUNSTABLE, msg);
+        }
     }
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();

@@ -107,6 +107,12 @@ cudaError_t launch_barrier_check(int grid, unsigned expect_blocks, int rounds, c
 // E0 + 13 |u|^2) for the n x n wave vectors of [-pi, pi]^2.  D = the derived
 // constants of lbm13_derive.  LBM13_EINVAL if an eigenvalue iteration fails.
 int linear_growth(const lbm13_params &p, const double *D, double ux, double uy, int n, double *growth);
+// The same scan for `count` cases at once on the GPU (stream s; synchronises
+// it): parameter set p[c] with derived constants D + c * LBM13_DERIVED_COUNT
+// about u = (ux[c], uy[c]); host out growth[count].  LBM13_EINVAL if an
+// eigenvalue iteration fails, LBM13_ECUDA on a CUDA error.
+int linear_growth_batch(const lbm13_params *p, const double *D, const double *ux, const double *uy, int count, int n,
+                        double *growth, cudaStream_t s);
 
 // Rest moments used by the read-outs (double precision).
 struct Rest {

@@ -40,7 +40,7 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
            "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
            "lbm13_plan_tma_check", "lbm13_fp64_fma_rate", "lbm13_plan_add", "lbm13_plan_remove",
-           "lbm13_halo_bytes", "lbm13_halo_pack", "lbm13_halo_unpack")
+           "lbm13_halo_bytes", "lbm13_halo_pack", "lbm13_halo_unpack", "lbm13_linear_growth_batch")
 
 
 class Lbm13Error(RuntimeError):
@@ -115,6 +115,7 @@ def lib():
         "lbm13_set_persistent": (C.c_int, [vp, C.c_int]),
         "lbm13_linear_growth": (C.c_int, [C.POINTER(Params), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]),
         "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
+        "lbm13_linear_growth_batch": (C.c_int, [C.POINTER(Params), dp, dp, C.c_int, C.c_int, dp, vp]),
         "lbm13_debug_violations": (C.c_int, [vp, C.POINTER(C.c_ulonglong)]),
         "lbm13_plan_tma_check": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "lbm13_time": (i64, [vp]),
@@ -182,6 +183,21 @@ def linear_growth(params, ux=0.0, uy=0.0, n=9):
     pp = make_params(params)
     _check(lib().lbm13_linear_growth(C.byref(pp), float(ux), float(uy), int(n), C.byref(out)))
     return out.value
+
+
+def linear_growth_batch(params_list, velocities, n=9, stream=None):
+    """max |z| - 1 of the linearised step for every (params_list[c],
+    velocities[c]) on an n x n k-grid, scanned on the current CUDA device."""
+    count = len(params_list)
+    if count != len(velocities) or count < 1:
+        raise ValueError("one velocity per parameter set, at least one case")
+    arr = (Params * count)(*[make_params(p) for p in params_list])
+    ux = np.ascontiguousarray([float(u[0]) for u in velocities])
+    uy = np.ascontiguousarray([float(u[1]) for u in velocities])
+    out = np.zeros(count)
+    _check(lib().lbm13_linear_growth_batch(arr, _dp(ux), _dp(uy), count, int(n), _dp(out),
+                                           C.c_void_p(stream.cuda_stream if stream is not None else 0)))
+    return out
 
 
 def barrier_check(blocks, extra_blocks, timeout_s):

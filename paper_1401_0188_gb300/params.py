@@ -80,11 +80,25 @@ def _heat_set_stable(nu, Pr):
     return nu <= (0.35 if Pr <= 0.71 else 0.2 if Pr <= 0.9 else 0.05)
 
 
-def select(nu, Pr, physical_heating=True):
+_SEARCHED = {}
+
+
+def _gpu_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
+
+
+def select(nu, Pr, physical_heating=True, search="auto"):
     """A free-parameter set that is linearly stable at (nu, Pr) for background
     speeds up to 0.03; with physical_heating (the default) the SET_HEAT family
-    wherever it is stable, else the sets above; ValueError outside their
-    ranges."""
+    wherever it is stable, else the sets above.  Outside their ranges, with
+    search = "auto" and a CUDA device (or search = True), the sets are searched
+    on demand by stability.search_batched (the batched GPU scan of the end of
+    Sec. 2) and the result kept for the process; ValueError when that finds no
+    stable set, or without a search."""
     from . import stability
     if physical_heating and _heat_set_stable(nu, Pr):
         return stability.make_params(SET_HEAT, nu, Pr, physical_heating=True)
@@ -94,6 +108,13 @@ def select(nu, Pr, physical_heating=True):
         return stability.make_params(SET_LOW_NU, nu, Pr)
     if 0.005 <= nu <= 0.03 and 0.5 <= Pr <= 0.95:
         return stability.make_params(SET_GAP, nu, Pr)
+    if search is True or (search == "auto" and _gpu_available()):
+        key = (round(nu, 12), round(Pr, 12), bool(physical_heating))
+        if key not in _SEARCHED:
+            p, g, _ = stability.search_batched(nu, Pr, physical_heating=physical_heating)
+            _SEARCHED[key] = p if g <= 1e-11 else None
+        if _SEARCHED[key] is not None:
+            return dict(_SEARCHED[key])
     raise ValueError(f"no stable parameter set known for nu = {nu}, Pr = {Pr}")
 
 

@@ -18,6 +18,10 @@ the thermal and viscous modes merge and the scheme tends to go unstable
 - `search(nu, Pr, ...)`: Nelder-Mead over the rest weights, c1, k2, c_varpiE
   and the four free rates, starting from a given set, until the scan is
   stable.  c_epsE follows the Prandtl number as in `params.pstar`.
+- `search_batched(nu, Pr, ...)`: the same procedure as a population search
+  whose candidates are all scanned in one batched call per generation
+  (`lbm13.linear_growth_batch` on the GPU by default: every candidate at every
+  background velocity and wave vector at once).
 """
 import numpy as np
 
@@ -170,3 +174,78 @@ def search(nu, Pr, U_max=0.03, start=PSTAR_RAW, n=17, maxiter=600, seed_scale=0.
                    options={"initial_simplex": np.array(simplex), "maxiter": maxiter, "xatol": 1e-6, "fatol": 0.0})
     best = make_params(res.x, nu, Pr, physical_heating)
     return best, max_growth(best, Ul, 25), res.x
+
+
+def _growth_in_batches(growth, plist, ulist):
+    """growth(plist, ulist) with a failing batch split until the failing
+    cases are isolated (their growth counts as 1: unusable)."""
+    from . import lbm13
+    try:
+        return np.asarray(growth(plist, ulist), dtype=float)
+    except lbm13.Lbm13Error:
+        if len(plist) == 1:
+            return np.array([1.0])
+        h = len(plist) // 2
+        return np.concatenate([_growth_in_batches(growth, plist[:h], ulist[:h]),
+                               _growth_in_batches(growth, plist[h:], ulist[h:])])
+
+
+def search_batched(nu, Pr, U_max=0.03, n=17, growth=None, starts=None, population=64, generations=40, seed=1,
+                   scale=0.05, physical_heating=False, tol=1e-11, verify_n=25, verify=None):
+    """Population search for a raw vector whose parameter set scans stable
+    (growth <= tol) at background speeds 0, U_max along x and along the
+    diagonal.  Each generation scans every candidate at the three speeds in
+    one call of `growth(params_list, velocities)` (default: the library's
+    batched GPU scan on an n x n k-grid), keeps the eight best and perturbs
+    them (seeded, relative steps of `scale`, shrinking).  A candidate that
+    scans stable is scanned again on the finer verify_n grid (`verify`, by
+    default the same batched scan), whose growth replaces its score: a coarse
+    grid can miss a narrow unstable band.  Returns (params, growth, raw) of
+    the first candidate stable on both grids, or of the best one found."""
+    from . import lbm13, params as _p
+    if growth is None:
+        growth = lambda pl, ul: lbm13.linear_growth_batch(pl, ul, n)  # noqa: E731
+        if verify is None:
+            verify = lambda pl, ul: lbm13.linear_growth_batch(pl, ul, verify_n)  # noqa: E731
+    Ul = ((0.0, 0.0), (U_max, 0.0), (U_max / np.sqrt(2), U_max / np.sqrt(2)))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if starts is None:
+        starts = [_p.SET_HEAT, _p.SET_HIGH_PR, _p.SET_GAP, _p.SET_LOW_NU, PSTAR_RAW]
+    pop = [np.array(x, dtype=float) for x in starts]
+    while len(pop) < population:
+        base = pop[len(pop) % len(starts)]
+        pop.append(base * (1.0 + scale * rng.standard_normal(base.shape)))
+    best = (None, np.inf, None)
+    for gen in range(generations):
+        cand, fit = [], np.full(len(pop), 1.0)
+        for i, raw in enumerate(pop):
+            rates = raw[7:11]
+            if (rates <= 0.02).any() or (rates >= 1.98).any() or (raw[:4] <= 0).any():
+                continue
+            p = make_params(raw, nu, Pr, physical_heating)
+            if derived(p)[0] != 0:
+                continue
+            cand.append((i, p))
+        if cand:
+            pl = [p for _, p in cand for _ in Ul]
+            ul = [u for _ in cand for u in Ul]
+            g = _growth_in_batches(growth, pl, ul).reshape(len(cand), len(Ul)).max(axis=1)
+            for (i, _), gi in zip(cand, g):
+                fit[i] = max(gi, 0.0)
+            passed = [(i, p) for (i, p), gi in zip(cand, g) if gi <= tol]
+            if passed and verify is not None:
+                pl = [p for _, p in passed for _ in Ul]
+                ul = [u for _ in passed for u in Ul]
+                gv = _growth_in_batches(verify, pl, ul).reshape(len(passed), len(Ul)).max(axis=1)
+                for (i, _), gi in zip(passed, gv):
+                    fit[i] = max(gi, 0.0)
+        order = np.argsort(fit, kind="stable")
+        if fit[order[0]] < best[1]:
+            best = (make_params(pop[order[0]], nu, Pr, physical_heating), float(fit[order[0]]), pop[order[0]].copy())
+        if best[1] <= tol:
+            break
+        elite = [pop[i] for i in order[:8]]
+        step = scale * (0.85 ** gen)
+        pop = elite + [elite[k % len(elite)] * (1.0 + step * rng.standard_normal(elite[0].shape))
+                       for k in range(population - len(elite))]
+    return best

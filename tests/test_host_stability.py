@@ -53,9 +53,9 @@ def test_pstar_unstable_near_unit_prandtl():
 
 def test_select_refuses_unknown_region():
     with pytest.raises(ValueError):
-        params.select(0.004, 0.95)
+        params.select(0.004, 0.95, search=False)
     with pytest.raises(ValueError):
-        params.select(0.006, 0.99)
+        params.select(0.006, 0.99, search=False)
     assert params.stable_viscosity(0.004, 0.95) == 0.005
     assert params.stable_viscosity(0.004, 0.99) == 0.01
 
@@ -87,3 +87,15 @@ def test_create_rejects_a_linearly_unstable_set():
     assert st == 3 and not h.value
     assert b"linearly unstable" in L.lbm13_last_error(None)
     assert lbm13.linear_growth(params.select(0.005, 0.71)) < 1e-12
+
+
+def test_batched_search_logic_with_the_host_scan():
+    """stability.search_batched with the numpy scan standing in for the GPU:
+    from pstar at Pr = 0.95 (unstable) and the tabulated sets it returns a set
+    that scans stable on a finer grid."""
+    def host_growth(plist, ulist):
+        return [stability.max_growth(p, (u,), 9) for p, u in zip(plist, ulist)]
+    p, g, raw = stability.search_batched(0.05, 0.95, growth=host_growth, starts=[stability.PSTAR_RAW, params.SET_HIGH_PR],
+                                         population=8, generations=3)
+    assert g <= 1e-11
+    assert stability.max_growth(p, UL, 21) < 1e-9
