@@ -383,8 +383,8 @@ int lbm13_plan_remove(lbm13_plan_t p, lbm13_t h);
 /* Autotuner: times every candidate (rows per thread R and warps per block BY
  * of the tile, row groups per tile 1, 4 or 16, persistent CTAs per SM or one
  * CTA per tile, and the order of the tiles: by lattice, round robin, largest
- * first: 180 candidates; FP32 plans also the ring-staged strips with 8, 16, 32
- * or 64 groups in the three orders: 12 more) over steps_per_candidate real
+ * first: 180 candidates; FP32 plans also the ring-staged strips of 64 and 32
+ * columns with 4, 8, 16 or 32 groups in the three orders: 24 more) over steps_per_candidate real
  * steps each (+1 warm-up), then keeps the fastest.  The steps taken count as
  * simulation steps.  *best_ms_per_step (may be NULL) gets the best time. */
 int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per_step);
@@ -395,14 +395,15 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
  * is 32 columns x groups * BY * R rows).  LBM13_EINVAL outside these.  In an
  * FP32 plan, (4,4) with one CTA per tile stages each tile's populations
  * through shared memory by tensor copies (TMA), 8 rows at a time; and
- * (R, BY) = (0, 8) (FP32 only; ctas_per_sm ignored) selects the ring-staged
- * strips: one CTA of eight warps per strip of 64 columns x groups 4-row groups,
- * whose input rows stream through a four-slot shared-memory ring by tensor
- * copies while the lattice's collision coefficients stay in registers. */
+ * (R, BY) = (0, 8) or (0, 4) (FP32 only; ctas_per_sm ignored) selects the
+ * ring-staged strips: one CTA of BY warps per strip of 8 BY columns x groups
+ * 4-row groups, whose input rows stream through a four-slot shared-memory ring
+ * by tensor copies while the lattice's collision coefficients stay in
+ * registers. */
 int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
 /* Self-check of the staged tiles' bounded wait (FP32 plan set to R = 4,
- * BY = 4, one CTA per tile, or to the ring-staged strips R = 0, BY = 8; else
+ * BY = 4, one CTA per tile, or to the ring-staged strips R = 0, BY = 8 or 4; else
  * LBM13_EINVAL): one staged launch with every
  * wait limited to timeout_s (1e-3 .. 2 s) and, when withhold != 0, no tensor
  * copy issued, so that every wait runs out and each block reports and leaves

@@ -1174,14 +1174,14 @@ bool encode_lattice_map(lbm13_t h, const void *buf, CUtensorMap *m)
 }
 
 // The same buffer ordered (x, plane, y) for the ring-staged strips: a box of
-// kRingX x 13 x kRingRows lands in shared memory as [row][plane][column].
-bool encode_ring_map(lbm13_t h, const void *buf, CUtensorMap *m)
+// box_x x 13 x kRingRows lands in shared memory as [row][plane][column].
+bool encode_ring_map(lbm13_t h, const void *buf, CUtensorMap *m, int box_x)
 {
     const EncodeTiled fn = tensor_map_encoder();
     if (!fn) return false;
     const cuuint64_t dims[3] = {cuuint64_t(h->nx), cuuint64_t(Q), cuuint64_t(h->ny)};
     const cuuint64_t strides[2] = {cuuint64_t(h->plane) * 4u, cuuint64_t(h->pitch) * 4u};
-    const cuuint32_t box[3] = {cuuint32_t(kRingX), cuuint32_t(Q), cuuint32_t(kRingRows)};
+    const cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(Q), cuuint32_t(kRingRows)};
     const cuuint32_t step[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(buf), dims, strides, box, step,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1199,9 +1199,12 @@ int plan_upload_maps(lbm13_plan_t p)
         const int cur = p->cur0[i];
         host[i].use = h->nx >= 64 && h->ny >= kTmaY && encode_lattice_map(h, h->buf[cur], &host[i].map[0]) &&
                       encode_lattice_map(h, h->buf[cur ^ 1], &host[i].map[1]);
-        host[i].ring_use = h->nx >= kRingW && h->ny >= kRingRows &&
-                           encode_ring_map(h, h->buf[cur], &host[i].ring[0]) &&
-                           encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring[1]);
+        host[i].ring_use = h->nx >= 64 && h->ny >= kRingRows &&
+                           encode_ring_map(h, h->buf[cur], &host[i].ring[0], Ring<64>::X) &&
+                           encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring[1], Ring<64>::X);
+        host[i].ring32_use = h->nx >= 32 && h->ny >= kRingRows &&
+                             encode_ring_map(h, h->buf[cur], &host[i].ring32[0], Ring<32>::X) &&
+                             encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring32[1], Ring<32>::X);
     }
     const size_t bytes = host.size() * sizeof(LatticeMaps);
     const size_t cap_bytes = std::max(p->cap, host.size()) * sizeof(LatticeMaps);
@@ -1232,8 +1235,11 @@ int plan_upload_map_one(lbm13_plan_t p, size_t i)
     const int cur = p->cur0[i];
     m.use = h->nx >= 64 && h->ny >= kTmaY && encode_lattice_map(h, h->buf[cur], &m.map[0]) &&
             encode_lattice_map(h, h->buf[cur ^ 1], &m.map[1]);
-    m.ring_use = h->nx >= kRingW && h->ny >= kRingRows && encode_ring_map(h, h->buf[cur], &m.ring[0]) &&
-                 encode_ring_map(h, h->buf[cur ^ 1], &m.ring[1]);
+    m.ring_use = h->nx >= 64 && h->ny >= kRingRows && encode_ring_map(h, h->buf[cur], &m.ring[0], Ring<64>::X) &&
+                 encode_ring_map(h, h->buf[cur ^ 1], &m.ring[1], Ring<64>::X);
+    m.ring32_use = h->nx >= 32 && h->ny >= kRingRows &&
+                   encode_ring_map(h, h->buf[cur], &m.ring32[0], Ring<32>::X) &&
+                   encode_ring_map(h, h->buf[cur ^ 1], &m.ring32[1], Ring<32>::X);
     cudaError_t e = cudaMemcpyAsync(static_cast<LatticeMaps *>(p->maps) + i, &m, sizeof m, cudaMemcpyHostToDevice,
                                     p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("tensor map upload: ") + cudaGetErrorString(e));
@@ -1288,14 +1294,16 @@ int plan_upload_descs(lbm13_plan_t p)
 // (tile row << 16) | tile column (both below 2^15 within the lattice limits),
 // in one of three orders: 0 lattice by lattice, 1 round robin across
 // lattices, 2 largest lattice first.
-bool plan_is_ring(const lbm13_plan *p) { return p->R == 0 && p->BY == 8; }
+bool plan_is_ring(const lbm13_plan *p) { return p->R == 0 && (p->BY == 8 || p->BY == 4); }
+// Strip width of the ring-staged shapes: eight warps take 64 columns, four 32.
+int plan_ring_width(const lbm13_plan *p) { return p->BY == 8 ? 64 : 32; }
 
 int plan_build_work(lbm13_plan_t p)
 {
-    // ring tiles: strips of kRingW columns x groups 4-row groups
+    // ring tiles: strips of 64 or 32 columns x groups 4-row groups
     const bool ring = plan_is_ring(p);
     const int rows = ring ? kRingRows * p->groups : p->R * p->BY * p->groups;
-    const int cols = ring ? kRingW : 32;
+    const int cols = ring ? plan_ring_width(p) : 32;
     const size_t L = p->lats.size();
     std::vector<std::vector<int2>> per(L);
     for (size_t i = 0; i < L; ++i) {
@@ -1343,7 +1351,7 @@ cudaError_t plan_launch(lbm13_plan_t p, int parity, cudaStream_t s)
         if (p->precision == LBM13_FP64 || !p->maps || !p->tma_err) return cudaErrorInvalidValue;
         return launch_batch_ring(static_cast<const BatchDesc<float, float> *>(p->desc),
                                  static_cast<const LatticeMaps *>(p->maps), static_cast<const int2 *>(p->work),
-                                 p->ntiles, parity, p->groups, p->tma_err, s);
+                                 p->ntiles, parity, p->groups, plan_ring_width(p), p->tma_err, s);
     }
     if (p->precision != LBM13_FP64 && p->R == 4 && p->BY == 4 && p->grid >= p->ntiles && p->maps && p->tma_err)
         return launch_batch_tma(static_cast<const BatchDesc<float, float> *>(p->desc),
@@ -1575,7 +1583,7 @@ int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int or
         groups < 1 || groups > 64)
         return pfail(p, LBM13_EINVAL, "unsupported tile shape, order, CTA count or row groups");
     if (R == 0 && p->precision == LBM13_FP64)
-        return pfail(p, LBM13_EINVAL, "the ring-staged tile shape (R = 0, BY = 8) is FP32 only");
+        return pfail(p, LBM13_EINVAL, "the ring-staged tile shapes (R = 0, BY = 8 or 4) are FP32 only");
     DeviceGuard g(p->device);
     p->R = R;
     p->BY = BY;
@@ -1593,7 +1601,7 @@ int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *ti
     if (p->precision == LBM13_FP64 || !p->maps || !p->tma_err ||
         !(ring || (p->R == 4 && p->BY == 4 && p->grid >= p->ntiles)))
         return pfail(p, LBM13_EINVAL,
-                     "the plan is not on staged FP32 tiles (R = 4, BY = 4, one CTA per tile; or the ring, R = 0, BY = 8)");
+                     "the plan is not on staged FP32 tiles (R = 4, BY = 4, one CTA per tile; or the ring, R = 0, BY = 8 or 4)");
     DeviceGuard g(p->device);
     int rc = plan_sync_parity(p);
     if (rc != LBM13_OK) return rc;
@@ -1602,8 +1610,8 @@ int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *ti
     const auto *maps = static_cast<const LatticeMaps *>(p->maps);
     const auto *work = static_cast<const int2 *>(p->work);
     const unsigned long long wait_ns = (unsigned long long)(timeout_s * 1e9);
-    cudaError_t e = ring ? launch_batch_ring(descs, maps, work, p->ntiles, p->parity, p->groups, p->tma_err, p->stream,
-                                             withhold ? 0 : 1, wait_ns)
+    cudaError_t e = ring ? launch_batch_ring(descs, maps, work, p->ntiles, p->parity, p->groups, plan_ring_width(p),
+                                             p->tma_err, p->stream, withhold ? 0 : 1, wait_ns)
                          : launch_batch_tma(descs, maps, work, p->ntiles, p->parity, p->groups, p->tma_err, p->stream,
                                             withhold ? 0 : 1, wait_ns);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -1691,11 +1699,13 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
         for (int c : ctas)
             for (int gr : groups)
                 for (int o = 0; o < 3; ++o) cands.push_back({sh[0], sh[1], c, gr, o});
-    // ring-staged strips (FP32): one block per strip segment of 4 groups rows
-    static const int ring_groups[] = {8, 16, 32, 64};
+    // ring-staged strips (FP32), 64 and 32 columns wide: one block per strip
+    // segment of 4 groups rows
+    static const int ring_groups[] = {4, 8, 16, 32};
     if (p->precision != LBM13_FP64)
-        for (int gr : ring_groups)
-            for (int o = 0; o < 3; ++o) cands.push_back({0, 8, 0, gr, o});
+        for (int by : {8, 4})
+            for (int gr : ring_groups)
+                for (int o = 0; o < 3; ++o) cands.push_back({0, by, 0, gr, o});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return pfail(p, LBM13_ECUDA, "cudaEventCreate");

@@ -318,9 +318,10 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar)
 }
 
 // One chunk: the box at (column x, plane 0, row y) of a map ordered (x, plane, y).
-__device__ __forceinline__ void ring_chunk(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar)
+__device__ __forceinline__ void ring_chunk(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar,
+                                           unsigned bytes)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRingBytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(dst), "l"(map), "r"(x), "r"(0), "r"(y), "r"(bar)
@@ -328,10 +329,12 @@ __device__ __forceinline__ void ring_chunk(unsigned dst, const CUtensorMap *map,
 }
 
 // Chunk k of the strip into its slot (the producer lane).
+template <int W>
 __device__ __forceinline__ void ring_issue(const CUtensorMap *map, unsigned st0, unsigned full0, int x0, int yb, int k)
 {
     const int slot = k % kRingSlots;
-    ring_chunk(st0 + unsigned(slot) * kRingBytes, map, x0 - 4, yb - 2 + kRingRows * k, full0 + 8u * slot);
+    ring_chunk(st0 + unsigned(slot) * Ring<W>::Bytes, map, x0 - 4, yb - 2 + kRingRows * k, full0 + 8u * slot,
+               Ring<W>::Bytes);
 }
 
 // Before the producer's warp leaves (normally or after a wait ran out), the
@@ -347,16 +350,17 @@ __device__ __forceinline__ void ring_drain(unsigned full0, int issued, unsigned 
 // ring row (input row of the node minus d) at the node's column (d = v_y in
 // -2 .. 2, index d + 2); link j reads plane j of ring row rb[v_y] at column
 // offset -v_x.
+template <int W>
 __device__ __forceinline__ void ring_pull(const float *const rb[5], float f[Q])
 {
 #pragma unroll
-    for (int j = 0; j < Q; ++j) f[j] = rb[cvy(j) + 2][j * kRingX - cvx(j)];
+    for (int j = 0; j < Q; ++j) f[j] = rb[cvy(j) + 2][j * Ring<W>::X - cvx(j)];
 }
 
 // Staged phase of a consumer warp: the nodes of its row that lie at least two
 // links from every edge, from the staged rows, with the coefficients in
 // registers and no out-of-line call.  Returns false after a wait ran out.
-template <bool Force>
+template <bool Force, int W>
 __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage, unsigned full0, unsigned empty0,
                              int x0, int yb, int ngroups, int wr, int half, const CUtensorMap *map, int producer,
                              unsigned *err, unsigned long long wait_ns)
@@ -379,7 +383,7 @@ __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage
             // has released that chunk
             const int c = g - 1;
             ok = mbar_wait(empty0 + 8u * (c % kRingSlots), unsigned((c / kRingSlots) & 1), wait_ns);
-            if (ok) ring_issue(map, st0, full0, x0, yb, issued++);
+            if (ok) ring_issue<W>(map, st0, full0, x0, yb, issued++);
         }
         if (g == 0) ok = ok && mbar_wait(full0, 0u, wait_ns);
         {
@@ -399,9 +403,9 @@ __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage
             const int r = kRingRows * g + wr + 2;
             const float *rb[5];
 #pragma unroll
-            for (int d = -2; d <= 2; ++d) rb[d + 2] = colp + ((r - d) & (kRingRowsTotal - 1)) * kRingRowFloats;
+            for (int d = -2; d <= 2; ++d) rb[d + 2] = colp + ((r - d) & (kRingRowsTotal - 1)) * Ring<W>::RowFloats;
             float f[Q];
-            ring_pull(rb, f);
+            ring_pull<W>(rb, f);
             collide<Force>(f, k);
 #ifdef LBM13_DEBUG
             store(a, x, y, f);
@@ -425,12 +429,12 @@ __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage
 // periodic wraps and the wall rules).  Every warp runs the same number of
 // iterations; lanes without a node pass x = nx, which neither loads out of the
 // lattice nor stores.
-template <bool Force>
+template <bool Force, int W>
 __device__ void ring_edges(const StepArgs<float, float> &a, int x0, int yb, int ngroups, int ctid, float *slot)
 {
-    constexpr int kT = 32 * kRingConsumers;
+    constexpr int kT = Ring<W>::Threads;
     const int nx = a.nx, ny = a.ny;
-    const int y_end = min(ny, yb + kRingRows * ngroups), x_end = min(nx, x0 + kRingW);
+    const int y_end = min(ny, yb + kRingRows * ngroups), x_end = min(nx, x0 + W);
     int er[4], ec[4], nr = 0, nc = 0;
     const int cy[4] = {0, 1, ny - 2, ny - 1}, cx[4] = {0, 1, nx - 2, nx - 1};
 #pragma unroll
@@ -445,8 +449,8 @@ __device__ void ring_edges(const StepArgs<float, float> &a, int x0, int yb, int 
         if (!dup_c && cx[i] >= x0 && cx[i] < x_end && cx[i] >= 0) ec[nc++] = cx[i];
     }
     // edge rows: 64 columns each, a warp on 32 consecutive columns of one row
-    for (int i = ctid; i < nr * kRingW; i += kT) {
-        const int r = i / kRingW, x = x0 + i % kRingW;
+    for (int i = ctid; i < nr * W; i += kT) {
+        const int r = i / W, x = x0 + i % W;
         process_column<float, float, Force, 1>(a, x < nx ? x : nx, er[r], slot);
     }
     // edge columns between the edge rows
@@ -461,18 +465,19 @@ __device__ void ring_edges(const StepArgs<float, float> &a, int x0, int yb, int 
     }
 }
 
-template <bool Force>
+template <bool Force, int W>
 __device__ __forceinline__ void ring_consume_row(int wr, const StepArgs<float, float> &a, const float *stage,
                                                  unsigned full0, unsigned empty0, int x0, int yb, int ngroups,
                                                  int half, const CUtensorMap *map, int producer, float *slot,
                                                  unsigned *err, unsigned long long wait_ns)
 {
     // the edge nodes first: their global loads overlap the first chunks' copies
-    ring_edges<Force>(a, x0, yb, ngroups, int(threadIdx.x), slot);
-    ring_consume<Force>(a, stage, full0, empty0, x0, yb, ngroups, wr, half, map, producer, err, wait_ns);
+    ring_edges<Force, W>(a, x0, yb, ngroups, int(threadIdx.x), slot);
+    ring_consume<Force, W>(a, stage, full0, empty0, x0, yb, ngroups, wr, half, map, producer, err, wait_ns);
 }
 
-__global__ void __launch_bounds__(kRingThreads, 2) batch_ring_kernel(const BatchDesc<float, float> *__restrict__ descs,
+template <int W>
+__global__ void __launch_bounds__(Ring<W>::Threads, Ring<W>::BlocksPerSm) batch_ring_kernel(const BatchDesc<float, float> *__restrict__ descs,
                                                                      const LatticeMaps *__restrict__ maps,
                                                                      const int2 *__restrict__ work, int parity,
                                                                      int groups, unsigned *err, int issue,
@@ -489,31 +494,31 @@ __global__ void __launch_bounds__(kRingThreads, 2) batch_ring_kernel(const Batch
     {
         const int4 *src = reinterpret_cast<const int4 *>(&descs[w.x].a[parity]);
         int4 *dst = reinterpret_cast<int4 *>(&sa);
-        for (int i = tid; i < kWords; i += kRingThreads) dst[i] = __ldg(src + i);
+        for (int i = tid; i < kWords; i += Ring<W>::Threads) dst[i] = __ldg(src + i);
     }
     const unsigned full0 = static_cast<unsigned>(__cvta_generic_to_shared(&bars[0]));
     const unsigned empty0 = full0 + 8u * kRingSlots;
     if (tid == 0) {
         s_force = descs[w.x].force;
-        s_use = maps[w.x].ring_use;
+        s_use = W == 64 ? maps[w.x].ring_use : maps[w.x].ring32_use;
         for (int i = 0; i < kRingSlots; ++i) {
             mbar_init_count(full0 + 8u * i, 1u);
-            mbar_init_count(empty0 + 8u * i, unsigned(kRingConsumers));
+            mbar_init_count(empty0 + 8u * i, unsigned(Ring<W>::Consumers));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const int x0 = (w.y & 0xffff) * kRingW;
+    const int x0 = (w.y & 0xffff) * W;
     const int yb = (w.y >> 16) * groups * kRingRows;
     const int ny = sa.ny;
     const int ngroups = min(groups, (ny - yb + kRingRows - 1) / kRingRows);
     float *stage = reinterpret_cast<float *>(ring_smem);
-    float *slots = stage + kRingSlots * kRingChunk;
+    float *slots = stage + kRingSlots * Ring<W>::Chunk;
     if (!s_use) {
         // a lattice without a ring tensor map: the warps step it through
         // global loads, one row per warp and group
-        const int x = x0 + 32 * (warp >> 2) + (tid & 31);
+        const int x = x0 + 32 * (warp >> 2) + (tid & 31);  // W / 32 slices x 4 rows
         for (int g = 0; g < ngroups; ++g) {
             const int y = yb + kRingRows * g + (warp & 3);
             if (y >= ny) break;
@@ -524,17 +529,17 @@ __global__ void __launch_bounds__(kRingThreads, 2) batch_ring_kernel(const Batch
         }
         return;
     }
-    const CUtensorMap *map = &maps[w.x].ring[parity];
+    const CUtensorMap *map = W == 64 ? &maps[w.x].ring[parity] : &maps[w.x].ring32[parity];
     const int producer = warp == 0 && issue;
     if (producer && (tid & 31) == 0) {
         const unsigned st0 = static_cast<unsigned>(__cvta_generic_to_shared(stage));
-        for (int k = 0; k < ngroups + 1 && k < kRingSlots; ++k) ring_issue(map, st0, full0, x0, yb, k);
+        for (int k = 0; k < ngroups + 1 && k < kRingSlots; ++k) ring_issue<W>(map, st0, full0, x0, yb, k);
     }
     if (s_force)
-        ring_consume_row<true>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
+        ring_consume_row<true, W>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
                                slots + tid * Q, err, wait_ns);
     else
-        ring_consume_row<false>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
+        ring_consume_row<false, W>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
                                 slots + tid * Q, err, wait_ns);
 }
 
@@ -554,7 +559,7 @@ cudaError_t launch_batch_rb(const BatchDesc<T, C> *descs, const int2 *work, int 
 bool batch_shape_supported(int R, int BY)
 {
     return (R == 1 && BY == 4) || (R == 2 && BY == 4) || (R == 4 && BY == 4) || (R == 2 && BY == 2) ||
-           (R == 1 && BY == 8) || (R == 0 && BY == 8);
+           (R == 1 && BY == 8) || (R == 0 && (BY == 8 || BY == 4));
 }
 
 template <typename T, typename C>
@@ -593,28 +598,40 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_ring(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
-                              int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue,
-                              unsigned long long wait_ns)
+template <int W>
+cudaError_t launch_ring_w(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work, int ntiles,
+                          int parity, int groups, unsigned *err, cudaStream_t s, int issue, unsigned long long wait_ns)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    if (groups < 1) return cudaErrorInvalidValue;
+    // the kernel's shared-memory allowance and carveout are per-device
+    // attributes: set them once on each device that launches it
     static std::atomic<unsigned long long> raised{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(raised.load() & bit)) {
-        e = cudaFuncSetAttribute(batch_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingSmem);
-        // two blocks per SM need the largest shared-memory carveout
+        e = cudaFuncSetAttribute(batch_ring_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, Ring<W>::Smem);
+        // several blocks per SM need the largest shared-memory carveout
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_ring_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(batch_ring_kernel<W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      int(cudaSharedmemCarveoutMaxShared));
         if (e != cudaSuccess) return e;
         raised.fetch_or(bit);
     }
-    batch_ring_kernel<<<ntiles, kRingThreads, kRingSmem, s>>>(descs, maps, work, parity, groups, err, issue, wait_ns);
+    batch_ring_kernel<W><<<ntiles, Ring<W>::Threads, Ring<W>::Smem, s>>>(descs, maps, work, parity, groups, err, issue,
+                                                                         wait_ns);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ring(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
+                              int ntiles, int parity, int groups, int width, unsigned *err, cudaStream_t s, int issue,
+                              unsigned long long wait_ns)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (groups < 1) return cudaErrorInvalidValue;
+    if (width == 64) return launch_ring_w<64>(descs, maps, work, ntiles, parity, groups, err, s, issue, wait_ns);
+    if (width == 32) return launch_ring_w<32>(descs, maps, work, ntiles, parity, groups, err, s, issue, wait_ns);
+    return cudaErrorInvalidValue;
 }
 
 template cudaError_t launch_batch<double, double>(const BatchDesc<double, double> *, const int2 *, int, int, int, int,

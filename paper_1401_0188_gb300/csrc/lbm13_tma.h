@@ -21,31 +21,36 @@ constexpr int kTmaStage = Q * kTmaY * kTmaX;              // floats per slab
 constexpr unsigned kTmaBytes = unsigned(kTmaStage) * 4u;   // bytes per slab
 constexpr int kTmaSmem = kTmaStage * 4;                    // one slab per block
 
-// Ring-staged tiles (batch_ring_kernel): a block of eight warps steps a
-// strip of 64 columns over `groups` 4-row output groups.  The strip's input
-// rows stream in 4-row chunks through a ring of kRingRowsTotal rows of shared
-// memory, laid out [ring row][plane][72 columns]: chunk k holds input rows
-// yb - 2 + 4k .. yb + 1 + 4k (columns x0 - 4 .. x0 + 67, so that its first
-// column is 16-byte aligned) in ring rows 4 (k mod kRingSlots) .. + 3, loaded
-// by one tensor copy whose map orders the lattice as (x, plane, y).  Output
-// group g (rows yb + 4g .. + 3) reads chunks g and g + 1 only, so with four
-// slots two chunks are in flight while two are read.  Each warp (two column
-// halves x four rows) steps one row of 32 nodes per group.  Full and empty
-// mbarriers per slot hand the chunks over; no block-wide barrier after the
-// set-up.  Two blocks per SM (16 warps).
-constexpr int kRingW = 64;
-constexpr int kRingX = kRingW + 8;
+// Ring-staged tiles (batch_ring_kernel): a block steps a strip of W columns
+// (W = 64 with eight warps, or W = 32 with four) over `groups` 4-row output
+// groups.  The strip's input rows stream in 4-row chunks through a ring of
+// kRingRowsTotal rows of shared memory, laid out [ring row][plane][W + 8
+// columns]: chunk k holds input rows yb - 2 + 4k .. yb + 1 + 4k (columns
+// x0 - 4 .. x0 + W + 3, so that its first column is 16-byte aligned) in ring
+// rows 4 (k mod kRingSlots) .. + 3, loaded by one tensor copy whose map orders
+// the lattice as (x, plane, y).  Output group g (rows yb + 4g .. + 3) reads
+// chunks g and g + 1 only, so with four slots two chunks are in flight while
+// two are read.  Each warp (W / 32 column slices x four rows) steps one row
+// of 32 nodes per group.  Full and empty mbarriers per slot hand the chunks
+// over; no block-wide barrier after the set-up.  W = 64: two blocks per SM,
+// W = 32: four (16 warps either way).
 constexpr int kRingRows = 4;
 constexpr int kRingSlots = 4;
 constexpr int kRingRowsTotal = kRingRows * kRingSlots;     // 16: ring row = relative row & 15
-constexpr int kRingRowFloats = Q * kRingX;                 // one ring row, all planes
-constexpr int kRingChunk = kRingRows * kRingRowFloats;     // floats per chunk
-constexpr unsigned kRingBytes = unsigned(kRingChunk) * 4u;  // bytes per chunk (14,976)
-constexpr int kRingConsumers = 8;
-constexpr int kRingThreads = 32 * kRingConsumers;
 static_assert((kRingRowsTotal & (kRingRowsTotal - 1)) == 0, "ring rows must be a power of two");
-// ring slots, then one 13-float row per thread for the edge gathers
-constexpr int kRingSmem = kRingSlots * int(kRingBytes) + kRingThreads * Q * 4;
+
+template <int W>
+struct Ring {
+    static constexpr int X = W + 8;                        // box width
+    static constexpr int Consumers = (W / 32) * kRingRows;  // warps
+    static constexpr int Threads = 32 * Consumers;
+    static constexpr int RowFloats = Q * X;                // one ring row, all planes
+    static constexpr int Chunk = kRingRows * RowFloats;    // floats per chunk
+    static constexpr unsigned Bytes = unsigned(Chunk) * 4u;
+    // ring slots, then one 13-float row per thread for the edge gathers
+    static constexpr int Smem = kRingSlots * int(Bytes) + Threads * Q * 4;
+    static constexpr int BlocksPerSm = W == 64 ? 2 : 4;
+};
 
 // One lattice's tensor maps: map[p] describes the buffer read when the step's
 // parity is p, as a 3-D tensor (x: nx, y: ny, plane: 13) with row stride
@@ -55,9 +60,11 @@ constexpr int kRingSmem = kRingSlots * int(kRingBytes) + kRingThreads * Q * 4;
 // could not be made).
 struct LatticeMaps {
     CUtensorMap map[2];
-    CUtensorMap ring[2];
+    CUtensorMap ring[2];    // boxes of the 64-column strips
+    CUtensorMap ring32[2];  // boxes of the 32-column strips
     int use;
     int ring_use;
+    int ring32_use;
 };
 
 // Staged batched step: one block per tile of 32 columns x 16 groups rows (two
@@ -71,13 +78,14 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
                              unsigned long long wait_ns = 1000000000ull);
 
 // Ring-staged batched step (FP32): one block per work item (lattice, strip of
-// 64 columns x groups 4-row groups), packed as (segment << 16) | strip.  Every
+// `width` = 64 or 32 columns x groups 4-row groups), packed as
+// (segment << 16) | strip.  Every
 // mbarrier wait is bounded by wait_ns of the global timer; after a timeout the
 // warp sets *err and leaves, and the producer lane waits (bounded) for the
 // copies it issued before it leaves.  issue = 0 withholds the copies (self-check of the
 // bounded waits; nothing is written then).
 cudaError_t launch_batch_ring(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
-                              int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue = 1,
-                              unsigned long long wait_ns = 1000000000ull);
+                              int ntiles, int parity, int groups, int width, unsigned *err, cudaStream_t s,
+                              int issue = 1, unsigned long long wait_ns = 1000000000ull);
 
 }  // namespace lbm13

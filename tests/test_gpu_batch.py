@@ -86,12 +86,13 @@ def test_every_configuration_is_bit_identical(L, precision):
     if precision == 1:
         # ring-staged strips: segments of 1 to 64 four-row groups (one group,
         # shorter and longer than the six-slot ring, and a whole lattice)
-        for order in (0, 1, 2):
-            for groups in (1, 2, 5, 6, 7, 16, 64):
-                plan.set_config(0, 8, 0, order, groups)
-                plan.step(3)
-                for g in b:
-                    g.step(3)
+        for BY in (8, 4):  # strips of 64 and 32 columns
+            for order in (0, 1, 2):
+                for groups in (1, 2, 5, 6, 7, 16, 64):
+                    plan.set_config(0, BY, 0, order, groups)
+                    plan.step(3)
+                    for g in b:
+                        g.step(3)
     else:
         with pytest.raises(L.Lbm13Error):
             plan.set_config(0, 8, 0, 0, 16)
@@ -99,7 +100,8 @@ def test_every_configuration_is_bit_identical(L, precision):
     plan.close()
 
 
-@pytest.mark.parametrize("precision,shape", [(0, (1, 4, 0, 2, 4)), (1, (1, 4, 0, 2, 4)), (1, (0, 8, 0, 2, 16))])
+@pytest.mark.parametrize("precision,shape", [(0, (1, 4, 0, 2, 4)), (1, (1, 4, 0, 2, 4)), (1, (0, 8, 0, 2, 16)),
+                                             (1, (0, 4, 0, 2, 16))])
 def test_admit_and_retire_keep_lattices_bit_identical(L, precision, shape):
     """lbm13_plan_add / lbm13_plan_remove: lattices join one at a time (past
     the table's first capacity, at different buffer parities, one just
@@ -169,16 +171,17 @@ def test_ring_strips_on_large_and_periodic_lattices(L):
             g.step(i % 2)
             group.append(g)
     plan = L.Plan(a)
-    for groups in (3, 16, 32):
-        plan.set_config(0, 8, 0, 2, groups)
-        plan.step(35)
-        for g in b:
-            g.step(35)
-        _same(a, b)
+    for BY in (8, 4):
+        for groups in (3, 16, 32):
+            plan.set_config(0, BY, 0, 2, groups)
+            plan.step(35)
+            for g in b:
+                g.step(35)
+            _same(a, b)
     plan.close()
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 1), (0, 8, 16)])
+@pytest.mark.parametrize("shape", [(4, 4, 1), (0, 8, 16), (0, 4, 16)])
 def test_staged_tile_wait_is_bounded(L, shape):
     """The staged (tensor-copy) tiles -- slabs and ring-staged strips -- wait on
     mbarriers with a time limit: with the copies withheld every wait runs out,
@@ -205,7 +208,7 @@ def test_tune_then_step(L):
     t0 = a[0].t
     best = plan.tune(2)
     c = plan.config()
-    assert best > 0 and c["tried"] == 192  # 180 register/slab tiles + 12 ring-staged strips
+    assert best > 0 and c["tried"] == 204  # 180 register/slab tiles + 24 ring-staged strips
     taken = a[0].t - t0
     assert taken == c["tried"] * 3
     plan.step(40)
