@@ -127,7 +127,7 @@ class Server:
 
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
                  max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config=(1, 4, 0, 2, 1),
-                 overlap=True, poll_s=0.0005):
+                 overlap=True, poll_s=0.0002):
         # plan_config: (R, BY, ctas_per_sm, order, groups) of the batched step
         self.plan_config = tuple(plan_config)
         self.backend = backend
@@ -183,7 +183,13 @@ class Server:
                     joining = self._admit(pending, active, joining, now, side)
                     if done_ev is None or not self.realtime or done_ev.query():
                         break
-                    time.sleep(self.poll_s)
+                    wait = pending[0].arrival - now() if pending else None
+                    if wait is None or wait <= 0:
+                        # nothing left to admit, or arrivals held back by the
+                        # slots or the budget until a retirement: wait for the round
+                        done_ev.synchronize()
+                        break
+                    time.sleep(min(self.poll_s, wait))
                 res = plan.residual(raise_on_divergence=False)
             else:
                 for a in active:
