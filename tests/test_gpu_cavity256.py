@@ -49,9 +49,9 @@ def _run(L, g, run, precision, steps=None):
         r = lat.residual()
         if (steps is not None and lat.t >= steps) or (steps is None and r[0] <= g["tol"]) or lat.t >= 3_000_000:
             break
-    fields = lat.macro()
+    fields, t = lat.macro(), lat.t
     lat.close()
-    return lat.t, r, fields
+    return t, r, fields
 
 
 def _samples(fields, run):
