@@ -125,11 +125,21 @@ class Server:
     the CUDA backend), new lattices are set up on a second stream while the
     current round runs."""
 
+    # tile shapes of the served plan, (R, BY, ctas_per_sm, order, groups): the
+    # one-row register tile while the plan is small, the 32-column ring-staged
+    # strips once it holds LARGE_PLAN_NODES nodes or more (measured faster there:
+    # p99 22.0 against 23.1 s on the fifth configuration's first 16 requests,
+    # slower on a trace of lattices up to 192^2); both give bit-identical steps
+    SMALL_PLAN = (1, 4, 0, 2, 1)
+    LARGE_PLAN = (0, 4, 0, 0, 8)
+    LARGE_PLAN_NODES = 1 << 20
+
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
-                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config=(1, 4, 0, 2, 1),
+                 max_steps=2_000_000, batched=True, realtime=True, backend=lbm13, plan_config="auto",
                  overlap=True, poll_s=0.0002):
-        # plan_config: (R, BY, ctas_per_sm, order, groups) of the batched step
-        self.plan_config = tuple(plan_config)
+        # plan_config: (R, BY, ctas_per_sm, order, groups) of the batched step,
+        # or "auto" (by the plan's node count, see SMALL_PLAN / LARGE_PLAN)
+        self.plan_config = plan_config if plan_config == "auto" else tuple(plan_config)
         self.backend = backend
         self.precision = precision
         self.hbm_budget = hbm_budget
@@ -155,16 +165,24 @@ class Server:
             side = torch.cuda.Stream()
         lattice_steps = 0
         joining = []     # admitted during the current round: join the next one
+        shape, changed = None, False   # the plan's tile shape; membership changed since set
         while pending or active or joining:
             # newly admitted lattices join the plan for this round
+            changed = changed or bool(joining)
             for a in joining:
                 if self.batched and plan is not None:
                     plan.add(a.lat)
                 active.append(a)
             if self.batched and joining and plan is None:
                 plan = self.backend.Plan([a.lat for a in active])
-                plan.set_config(*self.plan_config)
+                shape = None
             joining = []
+            if self.batched and plan is not None and (changed or shape is None):
+                want = self._shape(active)
+                if want != shape:
+                    plan.set_config(*want)
+                    shape = want
+            changed = False
             if not active:
                 joining = self._admit(pending, active, joining, now, side)
                 if not joining:
@@ -214,6 +232,8 @@ class Server:
                         else:
                             plan.close()
                             plan = None
+                        shape = None if plan is None else shape
+                        changed = True
                     a.lat.close()
                     self._used -= a.bytes
                 else:
@@ -229,6 +249,12 @@ class Server:
                    "precision": "fp64" if self.precision == lbm13.FP64 else "fp32-deviation",
                    "batched": self.batched, "overlap": side is not None}
         return sorted(results, key=lambda r: r.rid), summary
+
+    def _shape(self, active):
+        if self.plan_config != "auto":
+            return self.plan_config
+        nodes = sum(a.nx * a.ny for a in active)
+        return self.LARGE_PLAN if nodes >= self.LARGE_PLAN_NODES else self.SMALL_PLAN
 
     def _record(self, plan):
         """An event after the round just launched (None for stand-in plans)."""

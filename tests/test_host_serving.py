@@ -55,11 +55,17 @@ class FakeLattice:
 
 
 class FakePlan:
+    shapes = []   # (shape, nodes in the plan, plan) at every set_config
+
+    made = 0
+
     def __init__(self, lattices):
         self.lattices = list(lattices)
+        FakePlan.made += 1
+        self.serial = FakePlan.made
 
     def set_config(self, *a):
-        pass
+        FakePlan.shapes.append((a, sum(g.nx * g.ny for g in self.lattices), self.serial))
 
     def add(self, lat):
         assert all(g is not lat for g in self.lattices)
@@ -91,6 +97,7 @@ class Backend:
 def _reset():
     _Live.bytes = _Live.peak_bytes = _Live.count = _Live.peak_count = 0
     FakeLattice.diverge_at = {}
+    FakePlan.shapes = []
     yield
 
 
@@ -149,3 +156,26 @@ def test_request_above_the_budget_is_refused():
     reqs = _trace(2)
     with pytest.raises(ValueError):
         S.Server(lbm13.FP32_DEVIATION, hbm_budget=1000.0, check_every=100, realtime=False, backend=Backend).run(reqs)
+
+
+def test_plan_shape_follows_the_node_count():
+    """With plan_config "auto" the served plan takes the ring-staged strips
+    while it holds 2^20 nodes or more and the one-row tile below that, set
+    again whenever admission or retirement crosses the threshold."""
+    reqs = S.poisson_trace(10, rate=50.0, seed=7, side_range=(256, 1024), ra_range=(1e3, 1e5), tol=1e-3)
+    srv = S.Server(lbm13.FP32_DEVIATION, hbm_budget=1e12, max_slots=8, check_every=100, realtime=False,
+                   backend=Backend)
+    res, summary = srv.run(reqs)
+    assert summary["converged"] == len(reqs)
+    shapes = FakePlan.shapes
+    assert shapes and all(a == (S.Server.LARGE_PLAN if n >= S.Server.LARGE_PLAN_NODES else S.Server.SMALL_PLAN)
+                          for a, n, _ in shapes)
+    assert {a for a, _, _ in shapes} == {S.Server.LARGE_PLAN, S.Server.SMALL_PLAN}
+    # a plan is set again only when its shape changes
+    assert all(x[0] != y[0] for x, y in zip(shapes, shapes[1:]) if x[2] == y[2])
+    # a fixed shape is set once per plan and never changed
+    FakePlan.shapes = []
+    S.Server(lbm13.FP32_DEVIATION, hbm_budget=1e12, max_slots=8, check_every=100, realtime=False,
+             backend=Backend, plan_config=(1, 4, 0, 2, 1)).run(reqs)
+    assert {a for a, _, _ in FakePlan.shapes} == {(1, 4, 0, 2, 1)}
+    assert len({p for _, _, p in FakePlan.shapes}) == len(FakePlan.shapes)
