@@ -1090,6 +1090,9 @@ struct lbm13_plan {
     // block per tile) and the word their bounded waits set when one runs out
     void *maps = nullptr;
     size_t maps_bytes = 0;
+    // per lattice, the ring-staged maps made: bit 0 the 64-column strips',
+    // bit 1 the 32-column strips' (the edge work items follow them)
+    std::vector<unsigned char> ring_ok;
     unsigned *tma_err = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -1193,6 +1196,7 @@ bool encode_ring_map(lbm13_t h, const void *buf, CUtensorMap *m, int box_x)
 int plan_upload_maps(lbm13_plan_t p)
 {
     std::vector<LatticeMaps> host(p->lats.size());
+    p->ring_ok.assign(p->lats.size(), 0);
     for (size_t i = 0; i < p->lats.size(); ++i) {
         lbm13_t h = p->lats[i];
         std::memset(&host[i], 0, sizeof(LatticeMaps));
@@ -1205,6 +1209,7 @@ int plan_upload_maps(lbm13_plan_t p)
         host[i].ring32_use = h->nx >= 32 && h->ny >= kRingRows &&
                              encode_ring_map(h, h->buf[cur], &host[i].ring32[0], Ring<32>::X) &&
                              encode_ring_map(h, h->buf[cur ^ 1], &host[i].ring32[1], Ring<32>::X);
+        p->ring_ok[i] = (host[i].ring_use ? 1 : 0) | (host[i].ring32_use ? 2 : 0);
     }
     const size_t bytes = host.size() * sizeof(LatticeMaps);
     const size_t cap_bytes = std::max(p->cap, host.size()) * sizeof(LatticeMaps);
@@ -1240,6 +1245,8 @@ int plan_upload_map_one(lbm13_plan_t p, size_t i)
     m.ring32_use = h->nx >= 32 && h->ny >= kRingRows &&
                    encode_ring_map(h, h->buf[cur], &m.ring32[0], Ring<32>::X) &&
                    encode_ring_map(h, h->buf[cur ^ 1], &m.ring32[1], Ring<32>::X);
+    if (p->ring_ok.size() <= i) p->ring_ok.resize(i + 1, 0);
+    p->ring_ok[i] = (m.ring_use ? 1 : 0) | (m.ring32_use ? 2 : 0);
     cudaError_t e = cudaMemcpyAsync(static_cast<LatticeMaps *>(p->maps) + i, &m, sizeof m, cudaMemcpyHostToDevice,
                                     p->stream);
     if (e != cudaSuccess) return pfail(p, LBM13_ECUDA, std::string("tensor map upload: ") + cudaGetErrorString(e));
@@ -1293,7 +1300,11 @@ int plan_upload_descs(lbm13_plan_t p)
 // Work list for tiles of 32 columns x groups * BY * R rows, each packed as
 // (tile row << 16) | tile column (both below 2^15 within the lattice limits),
 // in one of three orders: 0 lattice by lattice, 1 round robin across
-// lattices, 2 largest lattice first.
+// lattices, 2 largest lattice first.  The ring-staged strips of a lattice with
+// ring maps step only the nodes two links or more from every edge; its edge
+// nodes (ring_edge_count, Ring<W>::EdgeNodes per item) come as items packed
+// -1 - item, ahead of its strips, so that their latency-bound global loads run
+// beside streaming strips.
 bool plan_is_ring(const lbm13_plan *p) { return p->R == 0 && (p->BY == 8 || p->BY == 4); }
 // Strip width of the ring-staged shapes: eight warps take 64 columns, four 32.
 int plan_ring_width(const lbm13_plan *p) { return p->BY == 8 ? 64 : 32; }
@@ -1310,6 +1321,12 @@ int plan_build_work(lbm13_plan_t p)
         lbm13_t h = p->lats[i];
         const int tx = (h->nx + cols - 1) / cols, ty = (h->ny + rows - 1) / rows;
         per[i].reserve(size_t(tx) * ty);
+        const unsigned bit = plan_ring_width(p) == 64 ? 1u : 2u;
+        if (ring && i < p->ring_ok.size() && (p->ring_ok[i] & bit)) {
+            const long long per_item = plan_ring_width(p) == 64 ? Ring<64>::EdgeNodes : Ring<32>::EdgeNodes;
+            const long long items = (ring_edge_count(h->nx, h->ny) + per_item - 1) / per_item;
+            for (long long e = 0; e < items; ++e) per[i].push_back(make_int2(int(i), int(-1 - e)));
+        }
         for (int y = 0; y < ty; ++y)
             for (int x = 0; x < tx; ++x) per[i].push_back(make_int2(int(i), (y << 16) | x));
     }
@@ -1468,6 +1485,7 @@ int plan_remove_one(lbm13_plan_t p, size_t i)
     if (i != last) {
         p->lats[i] = p->lats[last];
         p->cur0[i] = p->cur0[last];
+        if (last < p->ring_ok.size()) p->ring_ok[i] = p->ring_ok[last];
         auto *d = static_cast<BatchDesc<T, C> *>(p->desc);
         cudaError_t e = cudaMemcpyAsync(d + i, d + last, sizeof(BatchDesc<T, C>), cudaMemcpyDeviceToDevice, p->stream);
         if (e == cudaSuccess && sizeof(T) == 4 && p->maps) {
@@ -1478,6 +1496,7 @@ int plan_remove_one(lbm13_plan_t p, size_t i)
     }
     p->lats.pop_back();
     p->cur0.pop_back();
+    if (p->ring_ok.size() > p->lats.size()) p->ring_ok.resize(p->lats.size());
     return LBM13_OK;
 }
 

@@ -301,11 +301,15 @@ __global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float
 // releases chunk g when the group is done (group g + 1 reads chunks g + 1 and
 // g + 2).  The lattice's collision coefficients live in registers for the
 // whole strip; every warp runs the same code (the row within the group only
-// moves five ring-row addresses), and this phase makes no out-of-line call:
-// it steps only the nodes at least two links from every edge.  The block's
-// edge nodes come first, through process_column (periodic wraps and wall
-// rules) with global loads that overlap the first chunks' copies, so the
-// results are bit-identical to the other kernels.
+// moves five ring-row addresses), and the loop makes no out-of-line call: the
+// strips step only the nodes at least two links from every edge.  The edge
+// nodes are work items of their own in the same launch (ring_edge_item):
+// blocks that step them through process_column (periodic wraps and wall
+// rules) with global loads, latency-bound, beside strips that keep
+// streaming; the results are bit-identical to the other kernels.  (Edge work
+// inside the strips' loop, even from the staged rows, slowed every strip: it
+// costs the loop registers and instruction-cache room; a separate edge kernel
+// ran latency-bound on its own instead of beside the streams.)
 
 __device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count)
 {
@@ -423,57 +427,33 @@ __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage
     return true;
 }
 
-// Edge phase of the consumers: the nodes of the block's strip segment within two
-// links of an edge (rows 0, 1, ny-2, ny-1 across the strip; columns 0, 1,
-// nx-2, nx-1 in between), each through process_column with global loads (the
-// periodic wraps and the wall rules).  Every warp runs the same number of
-// iterations; lanes without a node pass x = nx, which neither loads out of the
-// lattice nor stores.
-template <bool Force, int W>
-__device__ void ring_edges(const StepArgs<float, float> &a, int x0, int yb, int ngroups, int ctid, float *slot)
+// An edge work item: nodes item * EdgeNodes .. (item + 1) * EdgeNodes - 1 of
+// the lattice's edge nodes (in ring_edge_count's order), one per thread,
+// through process_column with global loads.  Lanes past the last node pass
+// x = nx, which neither loads outside the lattice nor stores.
+template <int W>
+__device__ void ring_edge_item(const StepArgs<float, float> &a, int force, int item, float *slot)
 {
-    constexpr int kT = Ring<W>::Threads;
     const int nx = a.nx, ny = a.ny;
-    const int y_end = min(ny, yb + kRingRows * ngroups), x_end = min(nx, x0 + W);
-    int er[4], ec[4], nr = 0, nc = 0;
-    const int cy[4] = {0, 1, ny - 2, ny - 1}, cx[4] = {0, 1, nx - 2, nx - 1};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        bool dup_r = false, dup_c = false;
-#pragma unroll
-        for (int j = 0; j < i; ++j) {
-            dup_r = dup_r || cy[j] == cy[i];
-            dup_c = dup_c || cx[j] == cx[i];
-        }
-        if (!dup_r && cy[i] >= yb && cy[i] < y_end && cy[i] >= 0) er[nr++] = cy[i];
-        if (!dup_c && cx[i] >= x0 && cx[i] < x_end && cx[i] >= 0) ec[nc++] = cx[i];
+    const long long rows_part = 4LL * nx, total = ring_edge_count(nx, ny);
+    const long long i = (long long)item * Ring<W>::EdgeNodes + threadIdx.x;
+    int x = nx, y = min(2, ny - 1);
+    if (i < rows_part) {
+        // rows 0, 1, ny - 2, ny - 1
+        const int r = int(i / nx);
+        x = int(i - (long long)r * nx);
+        y = r < 2 ? r : ny - 4 + r;
+    } else if (i < total) {
+        // columns 0, 1, nx - 2, nx - 1 of rows 2 .. ny - 3
+        const long long k = i - rows_part;
+        const int c = int(k & 3);
+        y = 2 + int(k >> 2);
+        x = c < 2 ? c : nx - 4 + c;
     }
-    // edge rows: 64 columns each, a warp on 32 consecutive columns of one row
-    for (int i = ctid; i < nr * W; i += kT) {
-        const int r = i / W, x = x0 + i % W;
-        process_column<float, float, Force, 1>(a, x < nx ? x : nx, er[r], slot);
-    }
-    // edge columns between the edge rows
-    const int ylo = max(yb, 2), yhi = min(y_end, ny - 2);
-    const int n = nc * max(0, yhi - ylo);
-    const int nround = (n + 31) & ~31;
-    for (int i = ctid; i < nround; i += kT) {
-        const bool have = i < n;
-        const int x = have ? ec[i % nc] : nx;
-        const int y = have ? ylo + i / nc : ylo;
-        process_column<float, float, Force, 1>(a, x, y, slot);
-    }
-}
-
-template <bool Force, int W>
-__device__ __forceinline__ void ring_consume_row(int wr, const StepArgs<float, float> &a, const float *stage,
-                                                 unsigned full0, unsigned empty0, int x0, int yb, int ngroups,
-                                                 int half, const CUtensorMap *map, int producer, float *slot,
-                                                 unsigned *err, unsigned long long wait_ns)
-{
-    // the edge nodes first: their global loads overlap the first chunks' copies
-    ring_edges<Force, W>(a, x0, yb, ngroups, int(threadIdx.x), slot);
-    ring_consume<Force, W>(a, stage, full0, empty0, x0, yb, ngroups, wr, half, map, producer, err, wait_ns);
+    if (force)
+        process_column<float, float, true, 1>(a, x, y, slot);
+    else
+        process_column<float, float, false, 1>(a, x, y, slot);
 }
 
 template <int W>
@@ -509,12 +489,17 @@ __global__ void __launch_bounds__(Ring<W>::Threads, Ring<W>::BlocksPerSm) batch_
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    float *stage = reinterpret_cast<float *>(ring_smem);
+    float *slots = stage + kRingSlots * Ring<W>::Chunk;
+    if (w.y < 0) {
+        // an edge item (none in a check launch, whose copies are withheld)
+        if (issue) ring_edge_item<W>(sa, s_force, -1 - w.y, slots + tid * Q);
+        return;
+    }
     const int x0 = (w.y & 0xffff) * W;
     const int yb = (w.y >> 16) * groups * kRingRows;
     const int ny = sa.ny;
     const int ngroups = min(groups, (ny - yb + kRingRows - 1) / kRingRows);
-    float *stage = reinterpret_cast<float *>(ring_smem);
-    float *slots = stage + kRingSlots * Ring<W>::Chunk;
     if (!s_use) {
         // a lattice without a ring tensor map: the warps step it through
         // global loads, one row per warp and group
@@ -536,11 +521,11 @@ __global__ void __launch_bounds__(Ring<W>::Threads, Ring<W>::BlocksPerSm) batch_
         for (int k = 0; k < ngroups + 1 && k < kRingSlots; ++k) ring_issue<W>(map, st0, full0, x0, yb, k);
     }
     if (s_force)
-        ring_consume_row<true, W>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
-                               slots + tid * Q, err, wait_ns);
+        ring_consume<true, W>(sa, stage, full0, empty0, x0, yb, ngroups, warp & 3, warp >> 2, map, producer, err,
+                              wait_ns);
     else
-        ring_consume_row<false, W>(warp & 3, sa, stage, full0, empty0, x0, yb, ngroups, warp >> 2, map, producer,
-                                slots + tid * Q, err, wait_ns);
+        ring_consume<false, W>(sa, stage, full0, empty0, x0, yb, ngroups, warp & 3, warp >> 2, map, producer, err,
+                               wait_ns);
 }
 
 template <typename T, typename C, int R, int BY>

@@ -50,7 +50,18 @@ struct Ring {
     // ring slots, then one 13-float row per thread for the edge gathers
     static constexpr int Smem = kRingSlots * int(Bytes) + Threads * Q * 4;
     static constexpr int BlocksPerSm = W == 64 ? 2 : 4;
+    // nodes of one edge work item: one per thread of the block
+    static constexpr int EdgeNodes = Threads;
 };
+
+// The nodes of a lattice within two links of an edge, in the order the edge
+// work items of the ring-staged strips take them: rows 0, 1, ny - 2, ny - 1
+// across the lattice, then columns 0, 1, nx - 2, nx - 1 of rows 2 .. ny - 3
+// (four per row).  The strips step every other node from the staged rows.
+__host__ __device__ inline long long ring_edge_count(int nx, int ny)
+{
+    return 4LL * nx + 4LL * (ny > 4 ? ny - 4 : 0);
+}
 
 // One lattice's tensor maps: map[p] describes the buffer read when the step's
 // parity is p, as a 3-D tensor (x: nx, y: ny, plane: 13) with row stride
@@ -79,7 +90,9 @@ cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const Lattice
 
 // Ring-staged batched step (FP32): one block per work item (lattice, strip of
 // `width` = 64 or 32 columns x groups 4-row groups), packed as
-// (segment << 16) | strip.  Every
+// (segment << 16) | strip, or (lattice, edge item e) packed as -1 - e: its
+// share of the lattice's edge nodes (Ring<W>::EdgeNodes per item, in
+// ring_edge_count's order), stepped with global loads.  Every
 // mbarrier wait is bounded by wait_ns of the global timer; after a timeout the
 // warp sets *err and leaves, and the producer lane waits (bounded) for the
 // copies it issued before it leaves.  issue = 0 withholds the copies (self-check of the
