@@ -428,11 +428,22 @@ __device__ bool ring_consume(const StepArgs<float, float> &a, const float *stage
 }
 
 // An edge work item: nodes item * EdgeNodes .. (item + 1) * EdgeNodes - 1 of
-// the lattice's edge nodes (in ring_edge_count's order), one per thread,
-// through process_column with global loads.  Lanes past the last node pass
-// x = nx, which neither loads outside the lattice nor stores.
+// the lattice's edge nodes (in ring_edge_count's order), one per thread, each
+// link resolved on its own (gather_body compiled in, global loads: every load
+// of the node, its wall states' included, in one round trip), then collided
+// and stored.  Lanes past the last node have nothing to do; the halo rows of
+// a y-slab are written by the exchange, never stepped.
+template <bool Force>
+__device__ __forceinline__ void edge_node(const StepArgs<float, float> &a, int x, int y)
+{
+    float f[Q];
+    gather_body(a, x, y, f, GlobalInlineSrc<float, float>());
+    collide<Force>(f, a.k);
+    store(a, x, y, f);
+}
+
 template <int W>
-__device__ void ring_edge_item(const StepArgs<float, float> &a, int force, int item, float *slot)
+__device__ void ring_edge_item(const StepArgs<float, float> &a, int force, int item)
 {
     const int nx = a.nx, ny = a.ny;
     const long long rows_part = 4LL * nx, total = ring_edge_count(nx, ny);
@@ -450,10 +461,12 @@ __device__ void ring_edge_item(const StepArgs<float, float> &a, int force, int i
         y = 2 + int(k >> 2);
         x = c < 2 ? c : nx - 4 + c;
     }
+    if (x >= nx) return;
+    if ((y < 2 && a.wall[SOUTH].kind == HALO) || (y >= ny - 2 && a.wall[NORTH].kind == HALO)) return;
     if (force)
-        process_column<float, float, true, 1>(a, x, y, slot);
+        edge_node<true>(a, x, y);
     else
-        process_column<float, float, false, 1>(a, x, y, slot);
+        edge_node<false>(a, x, y);
 }
 
 template <int W>
@@ -493,7 +506,7 @@ __global__ void __launch_bounds__(Ring<W>::Threads, Ring<W>::BlocksPerSm) batch_
     float *slots = stage + kRingSlots * Ring<W>::Chunk;
     if (w.y < 0) {
         // an edge item (none in a check launch, whose copies are withheld)
-        if (issue) ring_edge_item<W>(sa, s_force, -1 - w.y, slots + tid * Q);
+        if (issue) ring_edge_item<W>(sa, s_force, -1 - w.y);
         return;
     }
     const int x0 = (w.y & 0xffff) * W;

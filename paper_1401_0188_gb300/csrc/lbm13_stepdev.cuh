@@ -49,6 +49,29 @@ __device__ __forceinline__ C ld(const StepArgs<T, C> &a, int j, int x, int y)
     return C(LBM13_LDG(chk(a, a.fin, a.fin + (long long)j * a.plane + (long long)y * a.pitch + x)));
 }
 
+// How the wall and edge code reads population j of node (x, y): from the
+// input buffer, with the wall-state code called out of line (GlobalSrc: the
+// step kernels, where edge nodes are a few lanes of a warp), or compiled into
+// the caller (GlobalInlineSrc: a kernel whose threads step edge nodes only,
+// so that every load of a node, the wall state's included, can be in flight
+// at once).  The values and the arithmetic are the same either way.
+template <typename T, typename C>
+struct GlobalSrc {
+    static constexpr bool kInline = false;
+    __device__ __forceinline__ C operator()(const StepArgs<T, C> &a, int j, int x, int y) const
+    {
+        return ld(a, j, x, y);
+    }
+};
+template <typename T, typename C>
+struct GlobalInlineSrc {
+    static constexpr bool kInline = true;
+    __device__ __forceinline__ C operator()(const StepArgs<T, C> &a, int j, int x, int y) const
+    {
+        return ld(a, j, x, y);
+    }
+};
+
 // ------------------------------------------------------ boundary links
 
 // Wall state (drho_w, dE_w): deviations of the wall's density and energy from
@@ -90,24 +113,22 @@ __device__ __forceinline__ WallState<C> zero_flux_state(const WallArgs<C> &w, C 
     return {drho, drho * w.base + w.eT + C(13) * rho * (w.ux * w.ux + w.uy * w.uy)};
 }
 
-// Wall state at position `pos` along side `s`.  Out of line: only the nodes
-// next to a wall that needs data evaluate it; returned by value so that the
-// caller keeps it in registers (no stack frame).
-template <typename T, typename C>
-__device__ __noinline__ WallState<C> wall_state(const StepArgs<T, C> &a, int s, int pos)
+// Wall state at position `pos` along side `s`.
+template <typename T, typename C, typename S>
+__device__ __forceinline__ WallState<C> wall_state_body(const StepArgs<T, C> &a, int s, int pos, S src)
 {
     const WallArgs<C> &w = a.wall[s];
     int x0, y0, x1, y1;
     wall_nodes(a, s, pos, x0, y0, x1, y1);
     if (w.kind == WALL_MIXED && w.mass_flux) {
         const int ja = out_unit(s), jb = out_two(s);
-        return zero_flux_state(w, ld(a, ja, x0, y0) + ld(a, jb, x0, y0) + ld(a, jb, x1, y1));
+        return zero_flux_state(w, src(a, ja, x0, y0) + src(a, jb, x0, y0) + src(a, jb, x1, y1));
     }
     C g0[Q], g1[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        g0[j] = ld(a, j, x0, y0);
-        g1[j] = ld(a, j, x1, y1);
+        g0[j] = src(a, j, x0, y0);
+        g1[j] = src(a, j, x1, y1);
     }
     const C drho = C(1.5) * mass_dev(g0) - C(0.5) * mass_dev(g1);
     const C rho = C(1) + drho;
@@ -117,6 +138,23 @@ __device__ __noinline__ WallState<C> wall_state(const StepArgs<T, C> &a, int s, 
     else
         dE = C(1.5) * energy_dev(g0) - C(0.5) * energy_dev(g1);
     return {drho, dE};
+}
+
+// Out of line: only the nodes next to a wall that needs data evaluate it;
+// returned by value so that the caller keeps it in registers (no stack frame).
+template <typename T, typename C>
+__device__ __noinline__ WallState<C> wall_state(const StepArgs<T, C> &a, int s, int pos)
+{
+    return wall_state_body(a, s, pos, GlobalSrc<T, C>());
+}
+
+template <typename T, typename C, typename S>
+__device__ __forceinline__ WallState<C> wall_state_of(const StepArgs<T, C> &a, int s, int pos, S src)
+{
+    if constexpr (S::kInline)
+        return wall_state_body(a, s, pos, src);
+    else
+        return wall_state(a, s, pos);
 }
 
 // a0 + a1 x + a2 y + a3 x^2 + a4 x y (a wall correction from the wall state).
@@ -146,8 +184,8 @@ __device__ __forceinline__ C cross_wall(const StepArgs<T, C> &a, int side, int j
 }
 
 // Every link of one node resolved on its own (warps on the bottom/top rows).
-template <typename T, typename C>
-__device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int y, C f[Q])
+template <typename T, typename C, typename S>
+__device__ __forceinline__ void gather_body(const StepArgs<T, C> &a, int x, int y, C f[Q], S src)
 {
     // Branch-free: every link's source offset and sign are chosen with
     // selects, so the 13 population loads are independent and in flight
@@ -165,8 +203,8 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
     const bool near_x = !px && (x <= 1 || x >= nx - 2), near_y = !py && (y <= 1 || y >= ny - 2);
     const bool corner_node = !px && !py && (x == 0 || x == nx - 1) && (y == 0 || y == ny - 1);
     WallState<C> stx = {C(0), C(0)}, sty = {C(0), C(0)};
-    if (near_x && (nd_x || (corner_node && nd_y))) stx = wall_state(a, sx_side, y);
-    if (near_y && (nd_y || (corner_node && nd_x))) sty = wall_state(a, sy_side, x);
+    if (near_x && (nd_x || (corner_node && nd_y))) stx = wall_state_of(a, sx_side, y, src);
+    if (near_y && (nd_y || (corner_node && nd_x))) sty = wall_state_of(a, sy_side, x, src);
     C v[Q];
     unsigned cross = 0u, neg = 0u, crx = 0u, cry = 0u;
 #pragma unroll
@@ -183,7 +221,7 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
         const int js = c ? copp(j) : j;
         const bool n = (ox && !oy && cvy(j) == 0 && kind_x == WALL_MIXED) ||
                        (oy && !ox && cvx(j) == 0 && kind_y == WALL_MIXED);
-        v[j] = C(LBM13_LDG(chk(a, a.fin, a.fin + (long long)js * a.plane + (long long)ys * a.pitch + xs)));
+        v[j] = src(a, js, xs, ys);
         cross |= (c ? 1u : 0u) << j;
         neg |= (n ? 1u : 0u) << j;
         crx |= (ox ? 1u : 0u) << j;
@@ -206,6 +244,12 @@ __device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int 
         const C w = ((neg >> j) & 1u) ? -v[j] : v[j];
         f[j] = ((cross >> j) & 1u) ? w + ad : v[j];
     }
+}
+
+template <typename T, typename C>
+__device__ __noinline__ void gather_general(const StepArgs<T, C> &a, int x, int y, C f[Q])
+{
+    gather_body(a, x, y, f, GlobalSrc<T, C>());
 }
 
 template <typename T, typename C>
