@@ -399,7 +399,9 @@ int lbm13_plan_tune(lbm13_plan_t p, int steps_per_candidate, double *best_ms_per
  * ring-staged strips: one CTA of BY warps per strip of 8 BY columns x groups
  * 4-row groups, whose input rows stream through a four-slot shared-memory ring
  * by tensor copies while the lattice's collision coefficients stay in
- * registers. */
+ * registers; the strips step the nodes two or more links from every edge, and
+ * each lattice's edge nodes are further CTAs of the same launch (one node per
+ * thread, global loads). */
 int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int order, int groups);
 
 /* Self-check of the staged tiles' bounded wait (FP32 plan set to R = 4,
@@ -407,7 +409,8 @@ int lbm13_plan_set_config(lbm13_plan_t p, int R, int BY, int ctas_per_sm, int or
  * LBM13_EINVAL): one staged launch with every
  * wait limited to timeout_s (1e-3 .. 2 s) and, when withhold != 0, no tensor
  * copy issued, so that every wait runs out and each block reports and leaves
- * without writing.  *timed_out = 1 when the error word was set (it is cleared
+ * without writing (the ring's edge-node CTAs, which do not wait, write nothing
+ * in such a launch either).  *timed_out = 1 when the error word was set (it is cleared
  * again).  The plan does not advance: the lattices keep their states. */
 int lbm13_plan_tma_check(lbm13_plan_t p, double timeout_s, int withhold, int *timed_out);
 
