@@ -272,7 +272,11 @@ int lbm13_barrier_check(int blocks, int extra_blocks, double timeout_s, int *tim
 /* Set the state to the equilibrium of the given fields (host arrays [ny][nx];
  * any NULL field takes its rest value: rho 1, u 0, T T0):
  * f*_j = f_eq,j(rho, j = rho u, E = rho (26 T - 28) + 13 rho |u|^2).
- * Resets the step counter and the residual snapshot. */
+ * Resets the step counter and the residual snapshot.  Returns when the state
+ * is set (synchronises).  A lattice of 2^22 nodes or more is uploaded in eight
+ * row bands on a second stream of the library's, each band's copies
+ * overlapping the set-up of the band before (host arrays in page-locked
+ * memory let the copies run asynchronously); the result is the same. */
 int lbm13_set_state(lbm13_t h, const double *rho, const double *ux, const double *uy, const double *T);
 
 /* As lbm13_set_state, with device arrays (no NULLs), stream-ordered. */
@@ -302,7 +306,9 @@ int lbm13_step(lbm13_t h, int64_t n);
 
 /* Selected moments/fields of the stored state (mask bits above), planes of
  * [ny][nx] doubles in increasing bit order, into a host buffer of
- * popcount(mask) * nx * ny doubles (synchronises). */
+ * popcount(mask) * nx * ny doubles (synchronises).  A lattice of 2^22 nodes
+ * or more is read out in eight row bands, each band's download (on a second
+ * stream) overlapping the computation of the next. */
 int lbm13_moments(lbm13_t h, double *out, unsigned mask);
 
 /* As lbm13_moments into a device buffer (stream-ordered, asynchronous). */

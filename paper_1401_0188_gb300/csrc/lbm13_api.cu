@@ -39,6 +39,10 @@ struct lbm13_lattice {
     // CUDA graphs of kGraphSteps steps, one per starting buffer parity
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // host transfers of large lattices in row bands: the copies on io_stream
+    // overlap the kernels of the neighbouring bands on `stream`
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t io_ev[2 * 8 + 1] = {};  // 2 kIoBands + 1
     // persistent multi-step launches: mode (LBM13_PERSISTENT_*), grid barrier
     // words (count, generation, error), grid size (0: not possible)
     int persistent = LBM13_PERSISTENT_AUTO;
@@ -354,6 +358,48 @@ ReadArgs<T> read_args(lbm13_t h)
     a.rho_ref = h->b.rho_ref;
     a.heat = h->b.heat;
     return a;
+}
+
+// The same for rows y0 .. y1 - 1 only (a band of a banded read-out).
+template <typename T>
+ReadArgs<T> read_args_rows(lbm13_t h, int y0, int y1)
+{
+    ReadArgs<T> a = read_args<T>(h);
+    a.f += (long long)y0 * h->pitch;
+    a.ny = y1 - y0;
+    return a;
+}
+
+// Host transfers of a lattice of kIoBandNodes nodes or more go in kIoBands row
+// bands, the copies on the lattice's I/O stream overlapping the kernels of the
+// neighbouring bands on its stream; smaller ones in one piece on its stream.
+constexpr long long kIoBandNodes = 1LL << 22;
+constexpr int kIoBands = 8;
+
+// Band count for a transfer (*nb), and for banded ones the I/O stream and
+// events (made on first use), the I/O stream ordered after the work already
+// on the lattice's stream.
+int io_prepare(lbm13_t h, int *nb)
+{
+    *nb = 1;
+    if ((long long)h->nx * h->ny < kIoBandNodes || h->ny < kIoBands) return LBM13_OK;
+    cudaError_t e = cudaSuccess;
+    if (!h->io_stream) e = cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t &ev : h->io_ev)
+        if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(h->io_ev[2 * kIoBands], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_stream, h->io_ev[2 * kIoBands], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "I/O stream set-up");
+    *nb = kIoBands;
+    return LBM13_OK;
+}
+
+// Wait for a transfer's copies and kernels on both streams; the first error.
+cudaError_t io_finish(lbm13_t h, int nb)
+{
+    cudaError_t a = nb > 1 ? cudaStreamSynchronize(h->io_stream) : cudaSuccess;
+    cudaError_t b = cudaStreamSynchronize(h->stream);
+    return a != cudaSuccess ? a : b;
 }
 
 template <typename T, typename C>
@@ -703,6 +749,12 @@ void lbm13_destroy(lbm13_t h)
     for (int i = 0; i < 2; ++i)
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->io_stream) {
+        cudaStreamSynchronize(h->io_stream);
+        cudaStreamDestroy(h->io_stream);
+    }
+    for (cudaEvent_t ev : h->io_ev)
+        if (ev) cudaEventDestroy(ev);
     for (int i = 0; i < 2; ++i) dev_free(h, h->buf[i], h->state_bytes);
     if (h->bad) dev_free(h, h->bad, sizeof(unsigned long long));
     if (h->red_mem) {
@@ -790,22 +842,48 @@ int lbm13_set_state(lbm13_t h, const double *rho, const double *ux, const double
     const size_t n = size_t(h->nx) * h->ny, bytes = n * sizeof(double);
     double *stage = static_cast<double *>(dev_alloc(h, 4 * bytes));
     if (!stage) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the state staging buffer");
-    const double *src[4] = {rho, ux, uy, T};
     const double rest[4] = {1.0, 0.0, 0.0, (h->p.E0 + 28.0) / 26.0};
-    int rc = LBM13_OK;
-    std::vector<double> fill;
-    for (int q = 0; q < 4 && rc == LBM13_OK; ++q) {
-        const double *s = src[q];
-        if (!s) {
-            fill.assign(n, rest[q]);
-            s = fill.data();
+    const double *src[4] = {rho, ux, uy, T};
+    std::vector<double> fill[4];  // absent fields: uniform, alive until the copies are done
+    for (int q = 0; q < 4; ++q)
+        if (!src[q]) {
+            fill[q].assign(n, rest[q]);
+            src[q] = fill[q].data();
         }
-        cudaError_t e = cudaMemcpyAsync(stage + q * n, s, bytes, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess && !src[q]) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaMemcpyAsync (state upload)");
+    int nb = 1;
+    int rc = io_prepare(h, &nb);
+    const int rows = (h->ny + nb - 1) / nb;
+    for (int b = 0; b < nb && rc == LBM13_OK; ++b) {
+        // band b: rows y0 .. y1 - 1 of the four fields, uploaded on the I/O
+        // stream (the first band's copies wait for the work already on the
+        // lattice's stream), then initialised on the lattice's stream
+        const int y0 = b * rows, y1 = std::min(h->ny, y0 + rows);
+        if (y0 >= y1) break;
+        const size_t off = size_t(y0) * h->nx, cnt = size_t(y1 - y0) * h->nx;
+        cudaStream_t cs = nb > 1 ? h->io_stream : h->stream;
+        cudaError_t e = cudaSuccess;
+        for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+            e = cudaMemcpyAsync(stage + q * n + off, src[q] + off, cnt * sizeof(double), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess && nb > 1) e = cudaEventRecord(h->io_ev[b], cs);
+        if (e == cudaSuccess && nb > 1) e = cudaStreamWaitEvent(h->stream, h->io_ev[b], 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "cudaMemcpyAsync (state upload)");
+            break;
+        }
+        e = h->precision == LBM13_FP64
+                ? launch_init<double>(static_cast<double *>(h->buf[h->cur]) + (long long)y0 * h->pitch, h->nx, y1 - y0,
+                                      h->pitch, h->plane, h->kd, stage + off, stage + n + off, stage + 2 * n + off,
+                                      stage + 3 * n + off, h->stream)
+                : launch_init<float>(static_cast<float *>(h->buf[h->cur]) + (long long)y0 * h->pitch, h->nx, y1 - y0,
+                                     h->pitch, h->plane, h->kd, stage + off, stage + n + off, stage + 2 * n + off,
+                                     stage + 3 * n + off, h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "init kernel launch");
     }
-    if (rc == LBM13_OK) rc = lbm13_set_state_device(h, stage, stage + n, stage + 2 * n, stage + 3 * n);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (rc == LBM13_OK) {
+        h->t = 0;
+        h->have_snap = 0;
+    }
+    cudaError_t e = io_finish(h, nb);
     if (rc == LBM13_OK && e != cudaSuccess) rc = cuda_fail(h, e, "cudaStreamSynchronize (set_state)");
     dev_free(h, stage, 4 * bytes);
     return rc;
@@ -922,18 +1000,38 @@ int lbm13_moments(lbm13_t h, double *out, unsigned mask)
     if (!h || !out) return fail(h, LBM13_EINVAL, "NULL argument");
     if (mask == 0 || (mask >> 18) != 0) return fail(h, LBM13_EINVAL, "mask must select bits 0..17");
     DeviceGuard g(h->device);
-    const size_t bytes = size_t(popcount18(mask)) * h->nx * h->ny * sizeof(double);
+    const int nf = popcount18(mask);
+    const size_t n = size_t(h->nx) * h->ny, bytes = size_t(nf) * n * sizeof(double);
     double *stage = static_cast<double *>(dev_alloc(h, bytes));
     if (!stage) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the moments staging buffer");
-    int rc = lbm13_moments_device(h, stage, mask);
-    if (rc == LBM13_OK) {
-        cudaError_t e = cudaMemcpyAsync(out, stage, bytes, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    int nb = 1;
+    int rc = io_prepare(h, &nb);
+    const int rows = (h->ny + nb - 1) / nb;
+    for (int b = 0; b < nb && rc == LBM13_OK; ++b) {
+        // band b: its fields computed on the lattice's stream into a block of
+        // the staging buffer laid out [field][rows][nx], then downloaded on
+        // the I/O stream while the next band is computed
+        const int y0 = b * rows, y1 = std::min(h->ny, y0 + rows);
+        if (y0 >= y1) break;
+        const size_t off = size_t(y0) * h->nx, cnt = size_t(y1 - y0) * h->nx;
+        double *blk = stage + off * nf;
+        cudaError_t e = h->precision == LBM13_FP64
+                            ? launch_moments<double>(read_args_rows<double>(h, y0, y1), blk, mask, h->stream)
+                            : launch_moments<float>(read_args_rows<float>(h, y0, y1), blk, mask, h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "moments kernel launch");
+            break;
+        }
+        cudaStream_t cs = nb > 1 ? h->io_stream : h->stream;
+        if (nb > 1) e = cudaEventRecord(h->io_ev[nb + b], h->stream);
+        if (e == cudaSuccess && nb > 1) e = cudaStreamWaitEvent(cs, h->io_ev[nb + b], 0);
+        for (int k = 0; k < nf && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(out + k * n + off, blk + k * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost, cs);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "moments download");
-        else rc = check_barrier_error(h);
-    } else {
-        cudaStreamSynchronize(h->stream);
     }
+    cudaError_t e = io_finish(h, nb);
+    if (rc == LBM13_OK && e != cudaSuccess) rc = cuda_fail(h, e, "moments download");
+    if (rc == LBM13_OK) rc = check_barrier_error(h);
     dev_free(h, stage, bytes);
     return rc;
 }

@@ -445,3 +445,36 @@ def test_staggered_invariant_at_size(L, pstar):
     assert abs(s0) > 1e-3
     assert abs(s1 - s0) <= 1e-13 * 15.0 * scale
     assert abs(r1 - r0) > 1e3 * abs(s1 - s0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_banded_transfers_equal_device_paths(L, pstar, prec):
+    """A lattice of 2^22 nodes or more uploads its fields and downloads its
+    read-outs in row bands, the copies overlapping the kernels of the other
+    bands: on a 2100 x 2050 lattice (ragged last band) the host paths give
+    exactly what the one-piece device paths give, populations and fields."""
+    import torch
+    nx, ny = 2100, 2050
+    T0 = _T0(pstar)
+    fields = W.random_fields(nx, ny, T0, seed=909, du=0.01, drho=0.005, dT=0.003)
+    a = L.Lattice(nx, ny, pstar, W.boundary(gx=1e-5), precision=prec)
+    b = L.Lattice(nx, ny, pstar, W.boundary(gx=1e-5), precision=prec)
+    a.set_state(*fields)
+    dev = [torch.as_tensor(np.ascontiguousarray(f, dtype=np.float64)).cuda() for f in fields]
+    torch.cuda.synchronize()
+    b.set_state_device(*dev)
+    b.synchronize()
+    assert np.array_equal(a.get_raw_state(), b.get_raw_state())
+    a.step(3)
+    mask = L.ALL_MOMENTS | L.FIELD_UX | L.FIELD_UY | L.FIELD_T | L.FIELD_P
+    host = a.moments(mask)
+    k = bin(mask).count("1")
+    out = torch.empty(k * nx * ny, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    a.moments_device(out, mask)
+    a.synchronize()
+    assert np.array_equal(host.reshape(-1), out.cpu().numpy())
+    a.close()
+    b.close()
+    del dev, out
+    torch.cuda.empty_cache()
