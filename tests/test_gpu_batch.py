@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1401_0188_gb300 import pstar as product_pstar
+from paper_1401_0188_gb300 import slabs
 from paper_1401_0188_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -26,14 +27,19 @@ def _specs():
     for i, (nx, ny, kind, nu, Pr) in enumerate([
             (64, 64, "cavity", 0.05, 0.71), (96, 70, "cavity", 0.03, 0.6), (37, 30, "couette", 0.05, 0.71),
             (40, 33, "poiseuille", 0.08, 0.8), (130, 45, "periodic", 0.02, 0.5), (4, 4, "box", 0.05, 0.71),
-            (200, 128, "cavity", 0.1, 0.9), (33, 257, "cavity", 0.04, 0.55), (48, 20, "slab", 0.05, 0.71)]):
+            (200, 128, "cavity", 0.1, 0.9), (33, 257, "cavity", 0.04, 0.55), (48, 20, "slab", 0.05, 0.71),
+            (96, 40, "slab_halos", 0.05, 0.71), (70, 36, "cavity_halo", 0.05, 0.71)]):
         p = product_pstar(nu, Pr)
         T0 = (p["E0"] + 28) / 26
         bnd = {"cavity": W.cavity(T0, 0.01, 1e-4), "couette": W.couette(T0, 0.02, 0.01),
                "poiseuille": W.poiseuille(1e-5), "periodic": W.boundary(gx=1e-5, gy=-2e-5),
                "box": W.boundary(west=W.wall(W.WALL_BB), east=W.wall(W.WALL_BB), south=W.wall(W.WALL_BB),
                                  north=W.wall(W.WALL_BB, 0.02)),
-               "slab": W.heated_slab(T0, 2e-6, 0.01)}[kind]
+               "slab": W.heated_slab(T0, 2e-6, 0.01),
+               # y-slabs of a decomposed lattice: halo rows on both sides, or
+               # below a walled top (halo rows are never stepped)
+               "slab_halos": slabs.slab_boundary(W.poiseuille(1e-5), True, True),
+               "cavity_halo": slabs.slab_boundary(W.cavity(T0, 0.01, 1e-4), True, False)}[kind]
         out.append((nx, ny, p, bnd, W.random_fields(nx, ny, T0, seed=100 + i, du=0.01, drho=0.005, dT=0.003)))
     return out
 
