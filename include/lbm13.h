@@ -260,6 +260,38 @@ int lbm13_info(lbm13_t h, int64_t out[8]);
 #define LBM13_PERSISTENT_ON 2
 int lbm13_set_persistent(lbm13_t h, int mode);
 
+/* Paired steps (FP32-deviation lattices periodic in x and y): lbm13_step
+ * advances such a lattice two time steps per launch when it steps n >= 2 (an
+ * odd n ends with one single step).  A paired launch reads the current buffer
+ * once and writes the state two steps later to the other buffer: persistent
+ * blocks take 28 x 28 tiles in turn, each stepping the tile and the two nodes
+ * around it in shared memory, then the tile, while the next tile's input
+ * arrives by tensor copy (the intermediate state never reaches HBM; DRAM
+ * traffic 52 bytes per update instead of 104, with 15% more collisions).
+ * Results are bit-identical to single steps.  AUTO (default): lattices of
+ * 2^21 nodes or more (smaller ones step faster singly); ON: every such
+ * lattice; OFF: one launch per step.  Every tensor copy's wait is bounded
+ * (1 s); a timeout is reported as LBM13_ETIMEOUT like a persistent launch's.
+ * Walled, slab (halo) and FP64 lattices, and persistent mode, step singly.
+ * LBM13_EINVAL for another mode. */
+#define LBM13_PAIR_AUTO 0
+#define LBM13_PAIR_OFF 1
+#define LBM13_PAIR_ON 2
+int lbm13_set_pair_steps(lbm13_t h, int mode);
+
+/* Kernel launches lbm13_step(h, n) makes with the lattice's current modes
+ * (n per-step launches, n / 2 rounded up paired ones, or one per 1024 steps
+ * of a persistent launch). */
+int lbm13_step_launches(lbm13_t h, int64_t n, int64_t *launches);
+
+/* Self-check of the paired steps' bounded wait: one paired launch from the
+ * current state with its wait limited to timeout_s (1e-3 .. 2 s) and, when
+ * withhold != 0, no tensor copy issued, so that every staged tile's wait runs
+ * out, reports and leaves without writing.  *timed_out = 1 when the error
+ * word was set (it is cleared again); the state and the step counter stay
+ * as they were.  LBM13_EINVAL for a lattice that does not take paired steps. */
+int lbm13_pair_check(lbm13_t h, double timeout_s, int withhold, int *timed_out);
+
 /* Self-check of the grid barrier's bounded wait on the current device: a
  * cooperative launch of `blocks` blocks runs 4 barriers that wait for
  * blocks + extra_blocks arrivals.  With extra_blocks = 0 every barrier

@@ -16,7 +16,7 @@ LIB = os.path.join(OUT, "liblbm13.so")
 # kernels is checked and counted (lbm13_debug_violations)
 DEBUG_OUT = os.path.join(HERE, "_build_debug")
 DEBUG_LIB = os.path.join(DEBUG_OUT, "liblbm13_debug.so")
-SOURCES = ["lbm13_step.cu", "lbm13_batch.cu", "lbm13_multi.cu", "lbm13_aux.cu", "lbm13_api.cu", "lbm13_noalloc.cu", "lbm13_linear.cu", "lbm13_probe.cu"]
+SOURCES = ["lbm13_step.cu", "lbm13_step2.cu", "lbm13_batch.cu", "lbm13_multi.cu", "lbm13_aux.cu", "lbm13_api.cu", "lbm13_noalloc.cu", "lbm13_linear.cu", "lbm13_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

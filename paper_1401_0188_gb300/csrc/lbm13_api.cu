@@ -43,6 +43,13 @@ struct lbm13_lattice {
     // overlap the kernels of the neighbouring bands on `stream`
     cudaStream_t io_stream = nullptr;
     cudaEvent_t io_ev[2 * 8 + 1] = {};  // 2 kIoBands + 1
+    // paired steps (FP32, periodic in x and y): mode (LBM13_PAIR_*), 1 once
+    // the tensor maps of both buffers are made, 0 when not possible, -1 not
+    // yet considered; graphs of kGraphSteps / 2 paired launches
+    int pair_mode = LBM13_PAIR_AUTO;
+    int pair_ok = -1;
+    CUtensorMap pair_map[2];
+    cudaGraphExec_t gexec2[2] = {nullptr, nullptr};
     // persistent multi-step launches: mode (LBM13_PERSISTENT_*), grid barrier
     // words (count, generation, error), grid size (0: not possible)
     int persistent = LBM13_PERSISTENT_AUTO;
@@ -454,18 +461,22 @@ GridSync grid_sync(lbm13_t h)
     return GridSync{w, w + 32, w + 64, kBarrierTimeoutNs};
 }
 
+// The step launches' error word and grid-barrier words (made on first use).
+bool ensure_sync_mem(lbm13_t h)
+{
+    if (h->sync_mem) return true;
+    h->sync_mem = dev_alloc(h, kSyncBytes);
+    if (!h->sync_mem) return false;
+    return cudaMemsetAsync(h->sync_mem, 0, kSyncBytes, h->stream) == cudaSuccess;
+}
+
 template <typename T, typename C>
 bool use_persistent(lbm13_t h, long long n)
 {
     if (h->persistent != LBM13_PERSISTENT_ON || n < 2) return false;
     if (h->multi_grid < 0) h->multi_grid = multi_grid<T, C>(h->nx, h->ny, h->force);
     if (h->multi_grid <= 0) return false;
-    if (!h->sync_mem) {
-        h->sync_mem = dev_alloc(h, kSyncBytes);
-        if (!h->sync_mem) return false;
-        if (cudaMemsetAsync(h->sync_mem, 0, kSyncBytes, h->stream) != cudaSuccess) return false;
-    }
-    return true;
+    return ensure_sync_mem(h);
 }
 
 // Reports (and clears) a grid-barrier timeout of an earlier persistent launch;
@@ -477,12 +488,90 @@ int check_barrier_error(lbm13_t h)
     CK(h, cudaMemcpy(&err, static_cast<unsigned *>(h->sync_mem) + 64, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (err == 0) return LBM13_OK;
     CK(h, cudaMemset(h->sync_mem, 0, kSyncBytes));
-    return fail(h, LBM13_ETIMEOUT, "a grid barrier of a persistent step launch timed out; the state is incomplete");
+    return fail(h, LBM13_ETIMEOUT,
+                "a bounded wait of a step launch (a persistent launch's grid barrier or a paired step's tensor copy) "
+                "timed out; the state is incomplete");
+}
+
+bool encode_pair_map(lbm13_t h, const void *buf, CUtensorMap *m);
+
+// Whether lbm13_step pairs its steps: FP32, periodic in x and y, not in
+// persistent mode, the tensor maps of both buffers made (once), and in AUTO
+// mode a lattice of kPairMinNodes nodes or more (below that the persistent
+// grid has too few tiles per block to hide each tile's copy: 256^2 and 512^2
+// step faster singly, 1024^2 alike, 2048^2 up 17%, 8192^2 up 34%).
+constexpr long long kPairMinNodes = 1LL << 21;
+
+bool use_pairs(lbm13_t h)
+{
+    if (h->pair_mode == LBM13_PAIR_OFF || h->precision == LBM13_FP64 || h->persistent == LBM13_PERSISTENT_ON ||
+        h->b.west.kind != PERIODIC || h->b.south.kind != PERIODIC)
+        return false;
+    if (h->pair_mode == LBM13_PAIR_AUTO && (long long)h->nx * h->ny < kPairMinNodes) return false;
+    if (h->pair_ok < 0)
+        h->pair_ok = encode_pair_map(h, h->buf[0], &h->pair_map[0]) && encode_pair_map(h, h->buf[1], &h->pair_map[1]);
+    return h->pair_ok == 1 && ensure_sync_mem(h);
+}
+
+unsigned *step_err(lbm13_t h) { return static_cast<unsigned *>(h->sync_mem) + 64; }
+
+// Captures kGraphSteps / 2 paired launches starting from buffer `cur`.
+cudaError_t build_pair_graph(lbm13_t h, int cur)
+{
+    cudaError_t e;
+    if (!h->cap_stream && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (long long i = 0; i < kGraphSteps / 2 && le == cudaSuccess; ++i) {
+        const int b = cur ^ int(i & 1);
+        le = launch_pair_step(step_args<float, float>(h, b, h->kf, h->wf), h->pair_map[b], h->force, step_err(h),
+                              h->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec2[cur], g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// n steps as paired launches (two steps each, the state's buffer flips at
+// every launch), replayed from graphs of kGraphSteps steps, and a single step
+// for an odd remainder.
+int do_pair_steps(lbm13_t h, long long n)
+{
+    if (n >= kGraphSteps) {
+        if (!h->gexec2[h->cur]) {
+            cudaError_t e = build_pair_graph(h, h->cur);
+            if (e != cudaSuccess) return cuda_fail(h, e, "paired-step graph capture");
+        }
+        for (; n >= kGraphSteps; n -= kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(h->gexec2[h->cur], h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch (paired steps)");
+            h->t += kGraphSteps;  // an even number of flips
+        }
+    }
+    for (; n >= 2; n -= 2) {
+        cudaError_t e = launch_pair_step(step_args<float, float>(h, h->cur, h->kf, h->wf), h->pair_map[h->cur],
+                                         h->force, step_err(h), h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "paired step launch");
+        h->cur ^= 1;
+        h->t += 2;
+    }
+    if (n == 1) {
+        cudaError_t e = launch_step<float, float>(step_args<float, float>(h, h->cur, h->kf, h->wf), h->force, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBM13_OK;
 }
 
 template <typename T, typename C>
 int do_steps(lbm13_t h, long long n, const Coef<C> &k, const WallArgs<C> *w)
 {
+    if (sizeof(T) == 4 && n >= 2 && use_pairs(h)) return do_pair_steps(h, n);
     if (use_persistent<T, C>(h, n)) {
         const GridSync g = grid_sync(h);
         while (n > 0) {
@@ -746,8 +835,10 @@ void lbm13_destroy(lbm13_t h)
     if (!h) return;
     DeviceGuard g(h->device);
     cudaStreamSynchronize(h->stream);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+        if (h->gexec2[i]) cudaGraphExecDestroy(h->gexec2[i]);
+    }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->io_stream) {
         cudaStreamSynchronize(h->io_stream);
@@ -784,6 +875,50 @@ int lbm13_info(lbm13_t h, int64_t out[8])
     out[5] = (int64_t)h->bytes_held;
     out[6] = h->t;
     out[7] = h->multi_grid > 0 ? h->multi_grid : 0;
+    return LBM13_OK;
+}
+
+int lbm13_step_launches(lbm13_t h, int64_t n, int64_t *launches)
+{
+    if (!h || !launches || n < 0) return fail(h, LBM13_EINVAL, "NULL argument or negative step count");
+    DeviceGuard g(h->device);
+    if (n >= 2 && h->precision != LBM13_FP64 && use_pairs(h))
+        *launches = n / 2 + (n & 1);
+    else if (n >= 2 && (h->precision == LBM13_FP64 ? use_persistent<double, double>(h, n)
+                                                     : use_persistent<float, float>(h, n)))
+        *launches = (n + kPersistentChunk - 1) / kPersistentChunk;
+    else
+        *launches = n;
+    return LBM13_OK;
+}
+
+int lbm13_set_pair_steps(lbm13_t h, int mode)
+{
+    if (!h) return fail(nullptr, LBM13_EINVAL, "NULL handle");
+    if (mode != LBM13_PAIR_AUTO && mode != LBM13_PAIR_OFF && mode != LBM13_PAIR_ON)
+        return fail(h, LBM13_EINVAL, "mode must be LBM13_PAIR_AUTO, LBM13_PAIR_OFF or LBM13_PAIR_ON");
+    h->pair_mode = mode;
+    return LBM13_OK;
+}
+
+int lbm13_pair_check(lbm13_t h, double timeout_s, int withhold, int *timed_out)
+{
+    if (!h || !timed_out || !(timeout_s >= 1e-3 && timeout_s <= 2.0))
+        return fail(h, LBM13_EINVAL, "NULL argument or timeout_s outside [1e-3, 2]");
+    DeviceGuard g(h->device);
+    if (!use_pairs(h)) return fail(h, LBM13_EINVAL, "the lattice does not take paired steps");
+    CK(h, cudaStreamSynchronize(h->stream));
+    int rc = check_barrier_error(h);
+    if (rc != LBM13_OK) return rc;
+    cudaError_t e = launch_pair_step(step_args<float, float>(h, h->cur, h->kf, h->wf), h->pair_map[h->cur], h->force,
+                                     step_err(h), h->stream, withhold ? 0 : 1,
+                                     (unsigned long long)(timeout_s * 1e9));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    unsigned word = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&word, step_err(h), sizeof word, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->sync_mem, 0, kSyncBytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "paired-step check");
+    *timed_out = word != 0u;
     return LBM13_OK;
 }
 
@@ -1283,6 +1418,21 @@ bool encode_ring_map(lbm13_t h, const void *buf, CUtensorMap *m, int box_x)
     const cuuint64_t dims[3] = {cuuint64_t(h->nx), cuuint64_t(Q), cuuint64_t(h->ny)};
     const cuuint64_t strides[2] = {cuuint64_t(h->plane) * 4u, cuuint64_t(h->pitch) * 4u};
     const cuuint32_t box[3] = {cuuint32_t(box_x), cuuint32_t(Q), cuuint32_t(kRingRows)};
+    const cuuint32_t step[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(buf), dims, strides, box, step,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The same buffer ordered (x, plane, y) in boxes of the paired steps' input
+// tile: kPairInX x 13 x kPairInY lands in shared memory as [row][plane][column].
+bool encode_pair_map(lbm13_t h, const void *buf, CUtensorMap *m)
+{
+    const EncodeTiled fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(h->nx), cuuint64_t(Q), cuuint64_t(h->ny)};
+    const cuuint64_t strides[2] = {cuuint64_t(h->plane) * 4u, cuuint64_t(h->pitch) * 4u};
+    const cuuint32_t box[3] = {cuuint32_t(kPairInX), cuuint32_t(Q), cuuint32_t(kPairInY)};
     const cuuint32_t step[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(buf), dims, strides, box, step,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

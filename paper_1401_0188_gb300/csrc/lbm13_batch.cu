@@ -7,6 +7,7 @@
 
 #include "lbm13_internal.h"
 #include "lbm13_tma.h"
+#include "lbm13_mbar.cuh"
 
 // Each launch reads only what earlier launches wrote: the read-only path.
 #define LBM13_LDG(p) __ldg(p)
@@ -113,48 +114,11 @@ __global__ void __launch_bounds__(32 * BY, sizeof(T) == 4 ? (R == 1 ? 32 / BY : 
 // rows within two of a y edge go through process_column itself, so the results
 // are bit-identical to the other kernels.
 
-__device__ __forceinline__ unsigned long long tma_clock()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
+__device__ __forceinline__ void mbar_init(unsigned bar) { mbar_init_count(bar, 1u); }
 
 __device__ __forceinline__ void tma_slab(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaBytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(0), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned phase)
-{
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    return done != 0;
-}
-
-// Wait for phase `phase` of the barrier to complete, for at most wait_ns (the
-// global timer is read only once the first try has failed).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, unsigned long long wait_ns)
-{
-    if (mbar_try(bar, phase)) return true;
-    const unsigned long long end = tma_clock() + wait_ns;
-    for (;;) {
-        if (mbar_try(bar, phase)) return true;
-        if (tma_clock() > end) return false;
-    }
+    tma_box_3d(dst, map, x, y, 0, bar, kTmaBytes);
 }
 
 // Row r of the slab in `tile` (its row 0 is the slab's first row minus 2,
@@ -311,25 +275,11 @@ __global__ void __launch_bounds__(128, 6) batch_tma_kernel(const BatchDesc<float
 // costs the loop registers and instruction-cache room; a separate edge kernel
 // ran latency-bound on its own instead of beside the streams.)
 
-__device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // One chunk: the box at (column x, plane 0, row y) of a map ordered (x, plane, y).
 __device__ __forceinline__ void ring_chunk(unsigned dst, const CUtensorMap *map, int x, int y, unsigned bar,
                                            unsigned bytes)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(map), "r"(x), "r"(0), "r"(y), "r"(bar)
-        : "memory");
+    tma_box_3d(dst, map, x, 0, y, bar, bytes);
 }
 
 // Chunk k of the strip into its slot (the producer lane).

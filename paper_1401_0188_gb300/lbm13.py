@@ -22,6 +22,7 @@ HALO_SOUTH, HALO_NORTH = 2, 3
 FP64, FP32_DEVIATION = 0, 1
 WALL_DENSITY_EXTRAPOLATE, WALL_DENSITY_ZERO_FLUX = 0, 1
 PERSISTENT_AUTO, PERSISTENT_OFF, PERSISTENT_ON = 0, 1, 2
+PAIR_AUTO, PAIR_OFF, PAIR_ON = 0, 1, 2
 DERIVED_COUNT = 48
 
 FIELD_UX, FIELD_UY, FIELD_T, FIELD_P, FIELD_E_SEC7 = 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17
@@ -40,7 +41,8 @@ EXPORTS = ("lbm13_version", "lbm13_status_string", "lbm13_derive", "lbm13_create
            "lbm13_plan_config", "lbm13_plan_residual", "lbm13_totals_noalloc", "lbm13_project",
            "lbm13_set_persistent", "lbm13_barrier_check", "lbm13_linear_growth", "lbm13_debug_violations",
            "lbm13_plan_tma_check", "lbm13_fp64_fma_rate", "lbm13_plan_add", "lbm13_plan_remove",
-           "lbm13_halo_bytes", "lbm13_halo_pack", "lbm13_halo_unpack", "lbm13_linear_growth_batch")
+           "lbm13_halo_bytes", "lbm13_halo_pack", "lbm13_halo_unpack", "lbm13_linear_growth_batch",
+           "lbm13_set_pair_steps", "lbm13_step_launches", "lbm13_pair_check")
 
 
 class Lbm13Error(RuntimeError):
@@ -113,6 +115,9 @@ def lib():
         "lbm13_residual": (C.c_int, [vp, dp]),
         "lbm13_project": (C.c_int, [vp, C.c_int, C.c_int, dp]),
         "lbm13_set_persistent": (C.c_int, [vp, C.c_int]),
+        "lbm13_set_pair_steps": (C.c_int, [vp, C.c_int]),
+        "lbm13_step_launches": (C.c_int, [vp, i64, C.POINTER(i64)]),
+        "lbm13_pair_check": (C.c_int, [vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "lbm13_linear_growth": (C.c_int, [C.POINTER(Params), C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]),
         "lbm13_barrier_check": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
         "lbm13_linear_growth_batch": (C.c_int, [C.POINTER(Params), dp, dp, C.c_int, C.c_int, dp, vp]),
@@ -417,6 +422,24 @@ class Lattice:
         """PERSISTENT_AUTO (default), PERSISTENT_OFF or PERSISTENT_ON: whether
         step(n) runs many steps per cooperative launch."""
         _check(lib().lbm13_set_persistent(self._h, int(mode)), self._h)
+
+    def set_pair_steps(self, mode):
+        """PAIR_AUTO (default: from 2^21 nodes), PAIR_ON or PAIR_OFF: whether
+        step(n) advances a lattice periodic in x and y (FP32-deviation) two
+        steps per launch."""
+        _check(lib().lbm13_set_pair_steps(self._h, int(mode)), self._h)
+
+    def step_launches(self, n):
+        """Kernel launches step(n) makes with the current modes."""
+        out = C.c_int64()
+        _check(lib().lbm13_step_launches(self._h, int(n), C.byref(out)), self._h)
+        return out.value
+
+    def pair_check(self, timeout_s, withhold=True):
+        """Self-check of the paired steps' bounded wait; True when it ran out."""
+        out = C.c_int()
+        _check(lib().lbm13_pair_check(self._h, float(timeout_s), int(bool(withhold)), C.byref(out)), self._h)
+        return bool(out.value)
 
     def project(self, kx, ky=0):
         """Fourier aggregates (Sec. 6): [field][harmonic][cos, sin] for the
