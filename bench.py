@@ -3,8 +3,10 @@
 Workload (one bench step = one time step of the whole lattice): the periodic
 transverse shear wave u_x = 0.01 sin(2 pi y / n) of the throughput sweep, at
 n x n = 8192 x 8192 by default, parameters nu = 0.05, Pr = 0.71, in
-FP32-deviation storage (104 algorithmic bytes per lattice update).  The FP64
-path (208 B/LU) is measured on the same lattice and reported beside it.
+FP32-deviation storage.  A lattice this size, periodic in x and y, takes two
+time steps per launch (52 algorithmic bytes per lattice update; 104 with one
+step per launch).  The FP64 path (208 B/LU) is measured on the same lattice
+and reported beside it.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload.
@@ -120,22 +122,27 @@ class Clocks:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def kernel_hash():
-    """Hash of the sources that define the step kernel (its launch, body and
-    arguments): a profile record only applies to the kernel it was taken on."""
+STEP_SOURCES = ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_stepdev.cuh", "lbm13_step.cu")
+PAIR_SOURCES = STEP_SOURCES + ("lbm13_tma.h", "lbm13_mbar.cuh", "lbm13_step2.cu")
+
+
+def kernel_hash(sources=STEP_SOURCES):
+    """Hash of the sources that define a kernel (its launch, body and
+    arguments; the single-step kernel by default, PAIR_SOURCES for the paired
+    one): a profile record only applies to the kernel it was taken on."""
     import hashlib
     src = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_stepdev.cuh", "lbm13_step.cu"):
+    for name in sources:
         with open(os.path.join(src, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profile_record(fname, tag):
+def profile_record(fname, tag, sources=STEP_SOURCES):
     """The value recorded under `tag` in profiles/<fname> ("tag hash value"
-    lines) if it was taken on the current step-kernel source; else None."""
-    digest = kernel_hash()
+    lines) if it was taken on the current source of its kernel; else None."""
+    digest = kernel_hash(sources)
     try:
         for line in open(os.path.join(ROOT, "profiles", fname)):
             parts = line.split()
@@ -149,6 +156,12 @@ def profile_record(fname, tag):
 def traffic_record(tag):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary."""
     return profile_record("step_kernel_traffic.txt", tag)
+
+
+def pair_record(tag):
+    """Per-launch figures of the paired-step kernel (DRAM bytes, warp
+    instructions per update) from its committed ncu summary."""
+    return profile_record("pair_step_kernel_records.txt", tag, PAIR_SOURCES)
 
 
 # Nominal FP64 rate of a GB300 (1.25 TFLOP/s at its 2070 MHz maximum SM
@@ -351,8 +364,10 @@ def run_sweep(args, torch, peak):
             lat.step(8)
             ms = time_steps(lat, steps, torch) / steps
             mlups = n * n / (ms / 1e3) / 1e6
-            out.append({"n": n, "precision": name, "MLUPS": mlups, "ms_per_step": ms,
-                        "hbm_frac": mlups * 1e6 * bl / 1e9 / peak, "state_MB": 2 * 13 * bl // 26 * n * n / 1e6})
+            paired = lat.step_launches(steps) < steps  # two steps per launch: half the bytes per update
+            out.append({"n": n, "precision": name, "MLUPS": mlups, "ms_per_step": ms, "paired": paired,
+                        "hbm_frac": mlups * 1e6 * (bl // 2 if paired else bl) / 1e9 / peak,
+                        "state_MB": 2 * 13 * bl // 26 * n * n / 1e6})
             lat.close()
             del lat
             torch.cuda.empty_cache()
@@ -430,12 +445,40 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     ms_max = max_over_ranks(ms, dev, world)
-    per_launch_s = ms / 1e3 / args.steps
+    per_step_s = ms / 1e3 / args.steps
     value = aggregate_mlups(n * n, args.steps, ms_max / 1e3, world)
     peak, peak_kind = measured_peaks()
-    achieved = bytes_lu * n * n / per_launch_s / 1e9
-    tag = f"step_{args.precision}_{n}"
-    traffic = traffic_record(tag)
+    launches = lat.step_launches(args.steps)
+    paired = launches < args.steps
+    if paired:
+        # two steps per launch: one read and one write of every population per
+        # two updates (52 B per update); the kernel is bound by instruction
+        # issue, so its roofline is the issue rate: 4 warp instructions per SM
+        # per clock at the SM clock sampled during the timed region
+        bytes_lu = 13 * elem
+        clocks = clk.summary() or {}
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = 4 * sms * sm_mhz * 1e6 / 1e9
+        ipl = pair_record(f"pair_{args.precision}_warp_instr_per_lu")
+        traffic = pair_record(f"pair_{args.precision}_{n}")
+        achieved_hbm = bytes_lu * n * n / per_step_s / 1e9
+        roofline = {
+            "bound": "alu", "unit": "G warp instr/s", "peak": issue_peak, "peak_kind": "derived",
+            "peak_basis": f"4 warp instructions per SM per clock x {sms} SMs x {sm_mhz:.0f} MHz (sampled)",
+            "achieved": None if ipl is None else ipl * n * n / per_step_s / 1e9,
+            "frac": None if ipl is None else ipl * n * n / per_step_s / 1e9 / issue_peak,
+            "instr_per_lu": ipl, "traffic": traffic,
+            "hbm": {"achieved": achieved_hbm, "peak": peak, "unit": "GB/s", "frac": achieved_hbm / peak,
+                    "bytes_per_lu": bytes_lu, "peak_kind": peak_kind},
+            "kernel": "pair_step_kernel (two fused steps per launch: 28x28 tiles, intermediate state in "
+                      "shared memory, persistent blocks, next tile by tensor copy)"}
+    else:
+        achieved = bytes_lu * n * n / per_step_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic_record(f"step_{args.precision}_{n}"),
+                    "peak_kind": peak_kind,
+                    "kernel": "step_kernel (fused pull-stream + walls + MRT collision)"}
 
     # end to end through the C ABI with host buffers: upload fields, step, read back
     e2e = None
@@ -539,12 +582,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
             "config": {"workload": f"periodic shear wave {n}x{n} (throughput sweep), u_x = 0.01 sin(2 pi y/n)",
                        "nu": NU, "Pr": PR, "precision": "fp32-deviation" if elem == 4 else "fp64",
-                       "bytes_per_lu": bytes_lu, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "bytes_per_lu": bytes_lu, "steps_per_launch": 2 if paired else 1, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({2 * 13 * elem * n * n / 1e9:.1f} GB of populations)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "step_kernel (fused pull-stream + walls + MRT collision)"},
-            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,
             "fp64": fp64,

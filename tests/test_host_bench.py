@@ -44,7 +44,7 @@ def test_profile_record_applies_only_to_its_kernel(tmp_path, monkeypatch):
                                   f"other_tag {digest} 5\n")
     # kernel_hash reads the sources under ROOT: point only the records elsewhere
     real_root = bench.ROOT
-    monkeypatch.setattr(bench, "kernel_hash", lambda: digest)
+    monkeypatch.setattr(bench, "kernel_hash", lambda sources=bench.STEP_SOURCES: digest)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.profile_record("rec.txt", "step_fp32_8192") == pytest.approx(6.94e9)
     assert bench.profile_record("rec.txt", "other_tag") == 5.0
