@@ -33,7 +33,7 @@ __device__ __forceinline__ bool pair_staged(int x0, int y0, int nx, int ny)
 // current one.  Each input buffer has its barrier; bit b of `phases` is the
 // parity buffer b's next completion will have (every thread tracks the same).
 template <bool Force>
-__global__ void __launch_bounds__(kPairThreads, 1)
+__global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
     pair_step_kernel(const StepArgs<float, float> a, const __grid_constant__ CUtensorMap map, unsigned *err,
                      int issue, unsigned long long wait_ns)
 {
@@ -160,7 +160,8 @@ cudaError_t launch_pair_step(const StepArgs<float, float> &a, const CUtensorMap 
         raised.fetch_or(bit);
     }
     const int ntiles = ((a.nx + kPairX - 1) / kPairX) * ((a.ny + kPairY - 1) / kPairY);
-    const int grid = ntiles < device_sm_count() ? ntiles : device_sm_count();
+    const int slots = kPairBlocksPerSm * device_sm_count();
+    const int grid = ntiles < slots ? ntiles : slots;
     if (force)
         pair_step_kernel<true><<<grid, kPairThreads, kPairSmem, s>>>(a, map, err, issue, wait_ns);
     else

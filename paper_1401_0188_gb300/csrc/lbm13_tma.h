@@ -82,6 +82,7 @@ constexpr int kPairIn = kPairInY * Q * kPairInX;     // floats of one input box
 constexpr int kPairInStride = (kPairIn + 31) / 32 * 32;  // input buffers 128 bytes apart
 constexpr int kPairMid = kPairMidY * Q * kPairMidX;  // floats
 constexpr int kPairThreads = 512;
+constexpr int kPairBlocksPerSm = 1;
 constexpr int kPairSmem = (2 * kPairInStride + kPairMid) * 4;  // 187,776 bytes: one block per SM
 static_assert(kPairMidX == 32, "the intermediate tile is one warp wide");
 // a tensor copy's shared-memory destination must be 128-byte aligned
