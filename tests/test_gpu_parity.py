@@ -301,12 +301,14 @@ def _tiled_fields(nx, ny, T0, seed):
     return rho, ux, uy, T
 
 
-@pytest.mark.parametrize("n,prec,steps", [(4096, 0, 2), (8192, 1, 2)])
+@pytest.mark.parametrize("n,prec,steps", [(4096, 0, 2), (8192, 1, 2), (8192, 1, 35)])
 def test_full_size_sampled_nodes_match_oracle(L, pstar, n, prec, steps):
     """Full-size periodic lattice in the bench's launch configuration: after
     `steps` steps, sampled nodes equal the oracle's result on the (4 steps + 1)^2
     patch of the same seeded fields around them (the dependence cone of a node
-    after `steps` pulls of reach 2)."""
+    after `steps` pulls of reach 2).  FP32 at 8192^2 takes paired steps: 2 is
+    one paired launch, 35 one 32-step graph of paired launches, one paired
+    launch and one single step."""
     import torch
     T0 = _T0(pstar)
     fields = _tiled_fields(n, n, T0, seed=31)
@@ -319,7 +321,7 @@ def test_full_size_sampled_nodes_match_oracle(L, pstar, n, prec, steps):
     r = 2 * steps
     rng = np.random.default_rng(77)
     pts = [(0, 0), (n - 1, n - 1), (n // 2, 3)] + [tuple(rng.integers(0, n, 2)) for _ in range(5)]
-    tol = TOL64 if prec == 0 else 2e-6
+    tol = TOL64 if prec == 0 else 2e-6 * max(1, steps // 8)
     for (x, y) in pts:
         xs = [(x + d) % n for d in range(-r, r + 1)]
         ys = [(y + d) % n for d in range(-r, r + 1)]
