@@ -333,7 +333,10 @@ int lbm13_save(lbm13_t h, void *host, size_t bytes);
 int lbm13_restore(lbm13_t h, const void *host, size_t bytes);
 
 /* Advance n >= 0 time steps: one fused stream + wall + collide kernel each,
- * launched on the lattice's stream (asynchronous). */
+ * launched on the lattice's stream (asynchronous); a large FP32 lattice
+ * periodic in x and y takes two steps per launch (lbm13_set_pair_steps), a
+ * lattice in persistent mode many (lbm13_set_persistent).  Runs of 32 steps
+ * are replayed from CUDA graphs. */
 int lbm13_step(lbm13_t h, int64_t n);
 
 /* Selected moments/fields of the stored state (mask bits above), planes of
