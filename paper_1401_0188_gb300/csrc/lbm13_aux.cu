@@ -47,7 +47,15 @@ struct NodeFields {
     double ux, uy, T, p;
 };
 
-template <typename T>
+// The read-out fields that need only the conserved moments (rho, E, j):
+// rho, E, j_x, j_y, u_x, u_y, T, p and the Sec. 7 energy.
+constexpr unsigned kConservedFields = (1u << 0) | (1u << 1) | (1u << 4) | (1u << 5) | (1u << 13) | (1u << 14) |
+                                      (1u << 15) | (1u << 16) | (1u << 17);
+
+// All 13 moments and the derived fields of a node; Conserved = true leaves the
+// nine non-conserved moments unset, so that their arithmetic is dropped (the
+// same code, so the conserved ones and the derived fields are identical).
+template <typename T, bool Conserved = false>
 __device__ __forceinline__ void node_fields(const ReadArgs<T> &a, long long idx, NodeFields &o)
 {
     double f[Q];
@@ -56,17 +64,19 @@ __device__ __forceinline__ void node_fields(const ReadArgs<T> &a, long long idx,
     forward(f, d);
     o.m[0] = 1.0 + d.rho;
     o.m[1] = a.rest.E0 + d.E;
-    o.m[2] = a.rest.eps0 + d.eps;
-    o.m[3] = a.rest.vpi0 + d.vpi;
     o.m[4] = d.jx;
     o.m[5] = d.jy;
-    o.m[6] = d.qx;
-    o.m[7] = d.qy;
-    o.m[8] = d.rx;
-    o.m[9] = d.ry;
-    o.m[10] = d.XX;
-    o.m[11] = d.XY;
-    o.m[12] = d.XXe;
+    if (!Conserved) {
+        o.m[2] = a.rest.eps0 + d.eps;
+        o.m[3] = a.rest.vpi0 + d.vpi;
+        o.m[6] = d.qx;
+        o.m[7] = d.qy;
+        o.m[8] = d.rx;
+        o.m[9] = d.ry;
+        o.m[10] = d.XX;
+        o.m[11] = d.XY;
+        o.m[12] = d.XXe;
+    }
     const double rho = o.m[0];
     const double w = rho - a.rho_ref;
     o.ux = (d.jx - 0.5 * w * a.gx) / rho;
@@ -82,7 +92,10 @@ __global__ void moments_kernel(const ReadArgs<T> a, double *__restrict__ out, un
     const int y = blockIdx.y;
     if (x >= a.nx) return;
     NodeFields o;
-    node_fields(a, (long long)y * a.pitch + x, o);
+    if ((mask & ~kConservedFields) == 0u)
+        node_fields<T, true>(a, (long long)y * a.pitch + x, o);
+    else
+        node_fields<T, false>(a, (long long)y * a.pitch + x, o);
     const long long n = (long long)a.nx * a.ny, i = (long long)y * a.nx + x;
     int plane = 0;
     for (int b = 0; b < 18; ++b) {

@@ -176,13 +176,22 @@ def test_macro_fields_and_residual_match_oracle(L, pstar):
     assert r_g[12] == 0.0
 
 
-def test_moment_mask_selects_planes(L, pstar):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_moment_mask_selects_planes(L, pstar, precision):
+    """A mask picks planes of the full read-out exactly, also when it asks only
+    for fields of the conserved moments (read out without the other nine)."""
     n = 40
-    g = L.Lattice(n, 24, pstar)
+    g = L.Lattice(n, 24, pstar, W.boundary(), precision=precision)
     g.set_state(*W.random_fields(n, 24, _T0(pstar), seed=3))
+    g.step(3)
     full = g.moments(L.ALL_MOMENTS | L.FIELD_UX | L.FIELD_UY | L.FIELD_T | L.FIELD_P | L.FIELD_E_SEC7)
     sub = g.moments((1 << 1) | (1 << 5) | L.FIELD_T)
     assert np.array_equal(sub, full[[1, 5, 15]])
+    cons = g.moments(1 | (1 << 1) | (1 << 4) | (1 << 5) | L.FIELD_UX | L.FIELD_UY | L.FIELD_T | L.FIELD_P
+                     | L.FIELD_E_SEC7)
+    assert np.array_equal(cons, full[[0, 1, 4, 5, 13, 14, 15, 16, 17]])
+    mixed = g.moments(1 | (1 << 6) | L.FIELD_T)
+    assert np.array_equal(mixed, full[[0, 6, 15]])
     rho, jx, jy, E = full[0], full[4], full[5], full[1]
     assert np.allclose(full[13], jx / rho, rtol=0, atol=1e-15)
     assert np.allclose(full[16], (E + 28 * rho) / 26 - (jx ** 2 + jy ** 2) / (2 * rho), atol=1e-14)
