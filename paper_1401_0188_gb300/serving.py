@@ -127,11 +127,13 @@ class Server:
 
     # tile shapes of the served plan, (R, BY, ctas_per_sm, order, groups): the
     # one-row register tile while the plan is small, the 32-column ring-staged
-    # strips once it holds LARGE_PLAN_NODES nodes or more (measured faster there:
-    # p99 22.0 against 23.1 s on the fifth configuration's first 16 requests,
-    # slower on a trace of lattices up to 192^2); both give bit-identical steps
+    # strips of 16 four-row groups once it holds LARGE_PLAN_NODES nodes or more
+    # (measured faster there, slower on a trace of lattices up to 192^2; on the
+    # fifth configuration's first 16 requests p99 19.2 s with 16 groups, 20.8 s
+    # with 8, the strips' best segment before their edge nodes became work
+    # items of their own); both give bit-identical steps
     SMALL_PLAN = (1, 4, 0, 2, 1)
-    LARGE_PLAN = (0, 4, 0, 0, 8)
+    LARGE_PLAN = (0, 4, 0, 0, 16)
     LARGE_PLAN_NODES = 1 << 20
 
     def __init__(self, precision=lbm13.FP32_DEVIATION, hbm_budget=120e9, max_slots=256, check_every=1000,
