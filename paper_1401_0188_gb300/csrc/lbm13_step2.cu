@@ -28,10 +28,14 @@ __device__ __forceinline__ bool pair_staged(int x0, int y0, int nx, int ny)
     return x0 >= 4 && x0 + kPairX + 4 <= nx && y0 >= 4 && y0 + kPairY + 4 <= ny;
 }
 
-// Persistent: block b takes tiles b, b + gridDim.x, ...; the tensor copy of
-// its next tile (into the other input buffer) is issued before it steps the
-// current one.  Each input buffer has its barrier; bit b of `phases` is the
-// parity buffer b's next completion will have (every thread tracks the same).
+// Persistent: block b takes tiles b, b + gridDim.x, ...; each tile's input
+// arrives by tensor copy into one of two buffers, issued as soon as the first
+// step of the tile two before it has freed that buffer, so each copy has
+// about a tile's time to land.  Each input buffer has its barrier; bit b of
+// `phases` is the parity buffer b's next completion will have (every thread
+// tracks the same).  Two block barriers per tile: after the first step (the
+// intermediate tile complete, the input buffer free, every wait agreed on)
+// and after the second (the intermediate tile free).
 template <bool Force>
 __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
     pair_step_kernel(const StepArgs<float, float> a, const __grid_constant__ CUtensorMap map, unsigned *err,
@@ -66,33 +70,24 @@ __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
     };
     unsigned phases = 0u;
     int k = 0;
+    // the first two tiles' copies; after that, the copy of the tile two on is
+    // issued as soon as the first step of the current tile has freed its buffer
     if (blockIdx.x < ntiles) fetch(blockIdx.x, 0);
+    if (blockIdx.x + gridDim.x < ntiles) fetch(blockIdx.x + gridDim.x, 1);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int b = k & 1;
         float *const in = pair_smem + b * kPairInStride;  // [kPairInY][Q][kPairInX], origin (x0 - 4, y0 - 4)
         const int x0 = (t % tx) * kPairX, y0 = (t / tx) * kPairY;
-        // the next tile's copy goes into the other buffer, free since the
-        // previous tile's last barrier
-        const int tn = t + gridDim.x;
-        const bool next_staged = tn < ntiles && pair_staged((tn % tx) * kPairX, (tn / tx) * kPairY, nx, ny);
-        if (tn < ntiles) fetch(tn, b ^ 1);
-        if (pair_staged(x0, y0, nx, ny)) {
-            const unsigned ph = (phases >> b) & 1u;
-            const bool ok = mbar_wait(bar0 + 8u * b, ph, wait_ns);
+        const bool staged = pair_staged(x0, y0, nx, ny);
+        bool ok = true;
+        unsigned ph = 0u;
+        if (staged) {
+            // every thread waits for the copy itself; the block agrees on the
+            // outcome at the barrier after the first step (nothing reaches
+            // global memory before it)
+            ph = (phases >> b) & 1u;
+            ok = mbar_wait(bar0 + 8u * b, ph, wait_ns);
             phases ^= 1u << b;
-            if (!__syncthreads_and(ok)) {
-                // a copy never landed within the limit: report, wait (bounded)
-                // for the copies this block issued so that none lands after it
-                // has left, and leave
-                if (tid == 0) {
-                    atomicOr(err, 1u);
-                    if (issue) {
-                        mbar_wait(bar0 + 8u * b, ph, wait_ns);
-                        if (next_staged) mbar_wait(bar0 + 8u * (b ^ 1), (phases >> (b ^ 1)) & 1u, wait_ns);
-                    }
-                }
-                return;
-            }
         } else {
             // a tile across the periodic seam: wrapped loads of the same box
             for (int i = tid; i < kPairIn; i += kPairThreads) {
@@ -114,7 +109,23 @@ __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
 #pragma unroll
             for (int j = 0; j < Q; ++j) mid[(iy * Q + j) * kPairMidX + ix] = f[j];
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            // a copy never landed within the limit: report, wait (bounded) for
+            // the copies this block issued (this tile's, the next tile's) so
+            // that none lands after it has left, and leave without writing
+            if (tid == 0) {
+                atomicOr(err, 1u);
+                if (issue) {
+                    if (staged) mbar_wait(bar0 + 8u * b, ph, wait_ns);
+                    const int tn = t + gridDim.x;
+                    if (tn < ntiles && pair_staged((tn % tx) * kPairX, (tn / tx) * kPairY, nx, ny))
+                        mbar_wait(bar0 + 8u * (b ^ 1), (phases >> (b ^ 1)) & 1u, wait_ns);
+                }
+            }
+            return;
+        }
+        // this input buffer is free: the copy of the tile two on goes into it
+        if (t + 2 * gridDim.x < ntiles) fetch(t + 2 * gridDim.x, b);
         // second step: the tile (28 lanes of each warp), to the other buffer
         for (int oy = warp; oy < kPairY; oy += kWarps) {
             const int ox = lane, x = x0 + ox, y = y0 + oy;
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
             for (int j = 0; j < Q; ++j) p[(long long)j * a.plane] = f[j];
 #endif
         }
-        __syncthreads();  // mid and this input buffer are free again
+        __syncthreads();  // the intermediate tile is free again
     }
 }
 
