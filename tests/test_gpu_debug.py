@@ -2,9 +2,10 @@
 every population load and store of the step kernels is checked against its
 lattice (plane, row and column in range) and counted when outside.  The
 parity shapes (ragged, tiny, every wall kind, forcing, energy source) in both
-storages, the persistent launch, and a plan stepped in every configuration
-(every tile shape including the tensor-copy one, grids, orders, row groups)
-must make no access outside their lattices."""
+storages, the persistent launch, paired steps of the periodic FP32 lattices,
+and a plan stepped in every configuration (every tile shape including the
+tensor-copy slabs and the ring-staged strips with their edge work items,
+grids, orders, row groups) must make no access outside their lattices."""
 import json
 import os
 import subprocess
@@ -39,6 +40,7 @@ cases = [
     (37, 30, W.couette(T0, 0.03, 0.01, wall_density=1)), (40, 24, W.heated_slab(T0, 1e-5, 0.02)),
     (130, 45, W.boundary(gx=1e-5, gy=-2e-5)), (200, 128, W.cavity(T0, 0.01, 1e-4, wall_density=1)),
     (1024, 8, W.boundary(south=W.wall(M, 0.01, hot), north=W.wall(B, -0.02), wall_density=1)),
+    (600, 400, W.boundary(gx=1e-5, gy=-2e-5)),
 ]
 lats = []
 for prec in (lbm13.FP64, lbm13.FP32_DEVIATION):
@@ -52,6 +54,13 @@ for g in lats[:6]:
     g.set_persistent(lbm13.PERSISTENT_ON)
     g.step(40)
 fp32 = [g for g in lats if g.precision == lbm13.FP32_DEVIATION]
+paired = 0
+for g in fp32:
+    # paired steps wherever the lattice takes them (periodic in x and y)
+    g.set_pair_steps(lbm13.PAIR_ON)
+    paired += g.step_launches(41) < 41
+    g.step(41)
+    g.set_pair_steps(lbm13.PAIR_AUTO)
 plan = lbm13.Plan(fp32)
 configs = 0
 for R, BY in ((1, 4), (2, 4), (4, 4), (2, 2), (1, 8)):
@@ -61,11 +70,17 @@ for R, BY in ((1, 4), (2, 4), (4, 4), (2, 2), (1, 8)):
                 plan.set_config(R, BY, ctas, order, groups)
                 plan.step(2)
                 configs += 1
+for BY in (8, 4):  # ring-staged strips and their edge work items
+    for order in (0, 2):
+        for groups in (1, 3, 16):
+            plan.set_config(0, BY, 0, order, groups)
+            plan.step(2)
+            configs += 1
 plan.step(33)
 plan.residual()
 plan.close()
 torch.cuda.synchronize()
-print(json.dumps({"lattices": len(lats), "configs": configs,
+print(json.dumps({"lattices": len(lats), "configs": configs, "paired": paired,
                   "violations": sum(g.debug_violations() for g in lats)}))
 """
 
@@ -81,5 +96,5 @@ def test_step_kernels_stay_inside_the_lattice():
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stderr[-3000:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    assert d["lattices"] == 34 and d["configs"] == 60
+    assert d["lattices"] == 36 and d["configs"] == 72 and d["paired"] >= 3
     assert d["violations"] == 0, d
