@@ -53,3 +53,16 @@ def test_profile_record_applies_only_to_its_kernel(tmp_path, monkeypatch):
     (prof / "stale.txt").write_text("step_fp32_8192 0123456789abcdef 1.0\n")
     assert bench.profile_record("stale.txt", "step_fp32_8192") is None
     assert os.path.isdir(os.path.join(real_root, "profiles"))
+
+
+def test_paired_kernel_records_follow_their_own_sources():
+    """The paired kernel's records are keyed by the hash of its own sources
+    (the single-step kernel's plus its file and headers), not the step hash."""
+    import bench
+    step, pair = bench.kernel_hash(), bench.kernel_hash(bench.PAIR_SOURCES)
+    assert step != pair and len(pair) == 16
+    assert set(bench.STEP_SOURCES) < set(bench.PAIR_SOURCES)
+    ipl = bench.pair_record("pair_fp32_warp_instr_per_lu")
+    assert ipl is None or 5.0 < ipl < 20.0
+    traffic = bench.pair_record("pair_fp32_8192")
+    assert traffic is None or traffic > 52 * 2 * 8192 * 8192  # at least the algorithmic bytes of a paired launch
