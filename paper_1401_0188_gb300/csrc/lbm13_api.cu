@@ -510,7 +510,7 @@ bool use_pairs(lbm13_t h)
     if (h->pair_mode == LBM13_PAIR_AUTO && (long long)h->nx * h->ny < kPairMinNodes) return false;
     if (h->pair_ok < 0)
         h->pair_ok = encode_pair_map(h, h->buf[0], &h->pair_map[0]) && encode_pair_map(h, h->buf[1], &h->pair_map[1]);
-    return h->pair_ok == 1 && ensure_sync_mem(h);
+    return h->pair_ok == 1;
 }
 
 unsigned *step_err(lbm13_t h) { return static_cast<unsigned *>(h->sync_mem) + 64; }
@@ -541,6 +541,7 @@ cudaError_t build_pair_graph(lbm13_t h, int cur)
 // for an odd remainder.
 int do_pair_steps(lbm13_t h, long long n)
 {
+    if (!ensure_sync_mem(h)) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the step error word");
     if (n >= kGraphSteps) {
         if (!h->gexec2[h->cur]) {
             cudaError_t e = build_pair_graph(h, h->cur);
@@ -907,6 +908,7 @@ int lbm13_pair_check(lbm13_t h, double timeout_s, int withhold, int *timed_out)
         return fail(h, LBM13_EINVAL, "NULL argument or timeout_s outside [1e-3, 2]");
     DeviceGuard g(h->device);
     if (!use_pairs(h)) return fail(h, LBM13_EINVAL, "the lattice does not take paired steps");
+    if (!ensure_sync_mem(h)) return fail(h, LBM13_ENOMEM, "allocator returned NULL for the step error word");
     CK(h, cudaStreamSynchronize(h->stream));
     int rc = check_barrier_error(h);
     if (rc != LBM13_OK) return rc;
