@@ -269,7 +269,7 @@ int lbm13_set_persistent(lbm13_t h, int mode);
  * arrives by tensor copy (the intermediate state never reaches HBM; DRAM
  * traffic 52 bytes per update instead of 104, with 15% more collisions).
  * Results are bit-identical to single steps.  AUTO (default): lattices of
- * 2^21 nodes or more (smaller ones step faster singly); ON: every such
+ * 2^20 nodes or more (smaller ones step faster singly); ON: every such
  * lattice; OFF: one launch per step.  Every tensor copy's wait is bounded
  * (1 s); a timeout is reported as LBM13_ETIMEOUT like a persistent launch's.
  * Walled, slab (halo) and FP64 lattices, and persistent mode, step singly.

@@ -498,9 +498,9 @@ bool encode_pair_map(lbm13_t h, const void *buf, CUtensorMap *m);
 // Whether lbm13_step pairs its steps: FP32, periodic in x and y, not in
 // persistent mode, the tensor maps of both buffers made (once), and in AUTO
 // mode a lattice of kPairMinNodes nodes or more (below that the persistent
-// grid has too few tiles per block to hide each tile's copy: 256^2 and 512^2
-// step faster singly, 1024^2 alike, 2048^2 up 17%, 8192^2 up 34%).
-constexpr long long kPairMinNodes = 1LL << 21;
+// grid has too few tiles per block to hide each tile's copy: 256^2 to 768^2
+// step faster singly; 1024^2 up 15%, 2048^2 up 25%, 8192^2 up 38%).
+constexpr long long kPairMinNodes = 1LL << 20;
 
 bool use_pairs(lbm13_t h)
 {

@@ -89,13 +89,39 @@ __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSm)
             ok = mbar_wait(bar0 + 8u * b, ph, wait_ns);
             phases ^= 1u << b;
         } else {
-            // a tile across the periodic seam: wrapped loads of the same box
-            for (int i = tid; i < kPairIn; i += kPairThreads) {
-                const int xx = i % kPairInX, r = i / kPairInX, j = r % Q, yy = r / Q;
-                int x = (x0 - 4 + xx) % nx, y = (y0 - 4 + yy) % ny;
-                x += x < 0 ? nx : 0;
-                y += y < 0 ? ny : 0;
-                in[i] = ld(a, j, x, y);
+            // a tile across the periodic seam: wrapped loads of the same box,
+            // kSeamBatch of them in flight per thread before the first is stored
+            // (a lattice at least one box wide and high wraps a coordinate with one
+            // add or subtract; smaller ones take the remainder)
+            constexpr int kPer = (kPairIn + kPairThreads - 1) / kPairThreads;
+            constexpr int kSeamBatch = 11;
+            const bool one_wrap = nx >= kPairInX && ny >= kPairInY;
+            for (int b0 = 0; b0 < kPer; b0 += kSeamBatch) {
+                float v[kSeamBatch];
+#pragma unroll
+                for (int u = 0; u < kSeamBatch; ++u) {
+                    const int i = tid + (b0 + u) * kPairThreads;
+                    v[u] = 0.0f;
+                    if (b0 + u < kPer && i < kPairIn) {
+                        const int xx = i % kPairInX, r = i / kPairInX, j = r % Q, yy = r / Q;
+                        int x = x0 - 4 + xx, y = y0 - 4 + yy;
+                        if (one_wrap) {
+                            x += x < 0 ? nx : (x >= nx ? -nx : 0);
+                            y += y < 0 ? ny : (y >= ny ? -ny : 0);
+                        } else {
+                            x %= nx;
+                            y %= ny;
+                            x += x < 0 ? nx : 0;
+                            y += y < 0 ? ny : 0;
+                        }
+                        v[u] = ld(a, j, x, y);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kSeamBatch; ++u) {
+                    const int i = tid + (b0 + u) * kPairThreads;
+                    if (b0 + u < kPer && i < kPairIn) in[i] = v[u];
+                }
             }
             __syncthreads();
         }

@@ -424,7 +424,7 @@ class Lattice:
         _check(lib().lbm13_set_persistent(self._h, int(mode)), self._h)
 
     def set_pair_steps(self, mode):
-        """PAIR_AUTO (default: from 2^21 nodes), PAIR_ON or PAIR_OFF: whether
+        """PAIR_AUTO (default: from 2^20 nodes), PAIR_ON or PAIR_OFF: whether
         step(n) advances a lattice periodic in x and y (FP32-deviation) two
         steps per launch."""
         _check(lib().lbm13_set_pair_steps(self._h, int(mode)), self._h)

@@ -83,11 +83,11 @@ def test_walled_slab_and_fp64_lattices_step_singly(L):
         g.set_pair_steps(L.PAIR_ON)
         assert g.step_launches(10) == 10
         g.close()
-    # AUTO pairs from 2^21 nodes on
-    g = L.Lattice(1024, 1024, p, W.boundary(), precision=L.FP32_DEVIATION)
+    # AUTO pairs from 2^20 nodes on
+    g = L.Lattice(768, 768, p, W.boundary(), precision=L.FP32_DEVIATION)
     assert g.step_launches(10) == 10
     g.close()
-    g = L.Lattice(2048, 1024, p, W.boundary(), precision=L.FP32_DEVIATION)
+    g = L.Lattice(1024, 1024, p, W.boundary(), precision=L.FP32_DEVIATION)
     assert g.step_launches(10) == 5
     g.close()
     g = L.Lattice(64, 40, p, W.boundary(), precision=L.FP32_DEVIATION)
