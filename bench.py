@@ -123,7 +123,7 @@ class Clocks:
 
 
 STEP_SOURCES = ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_stepdev.cuh", "lbm13_step.cu")
-PAIR_SOURCES = STEP_SOURCES + ("lbm13_tma.h", "lbm13_mbar.cuh", "lbm13_step2.cu")
+PAIR_SOURCES = STEP_SOURCES + ("lbm13_pair.h", "lbm13_mbar.cuh", "lbm13_step2.cu")
 
 
 def kernel_hash(sources=STEP_SOURCES):

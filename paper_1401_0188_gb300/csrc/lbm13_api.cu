@@ -13,6 +13,7 @@
 #include "../../include/lbm13.h"
 #include "lbm13_internal.h"
 #include "lbm13_tma.h"
+#include "lbm13_pair.h"
 
 using namespace lbm13;
 

@@ -13,7 +13,7 @@
 #include <atomic>
 
 #include "lbm13_internal.h"
-#include "lbm13_tma.h"
+#include "lbm13_pair.h"
 #include "lbm13_mbar.cuh"
 
 #define LBM13_LDG(p) __ldg(p)

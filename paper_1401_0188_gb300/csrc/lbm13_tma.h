@@ -1,5 +1,6 @@
 // lbm13_tma.h -- tensor-map staging of the batched FP32 step (lbm13_batch.cu)
-// and its host-side description (lbm13_api.cu).
+// and its host-side description (lbm13_api.cu).  The paired steps' tile
+// constants are in lbm13_pair.h.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (the type only: the encoder is fetched through the runtime)
@@ -32,8 +33,9 @@ constexpr int kTmaSmem = kTmaStage * 4;                    // one slab per block
 // chunks g and g + 1 only, so with four slots two chunks are in flight while
 // two are read.  Each warp (W / 32 column slices x four rows) steps one row
 // of 32 nodes per group.  Full and empty mbarriers per slot hand the chunks
-// over; no block-wide barrier after the set-up.  W = 64: two blocks per SM,
-// W = 32: four (16 warps either way).
+// over; no block-wide barrier after the set-up.  W = 64: two blocks per SM
+// (16 warps), W = 32: five (20 warps, the register cap 96, which the strips
+// meet without spilling; six blocks would cap it at 80 and spill).
 constexpr int kRingRows = 4;
 constexpr int kRingSlots = 4;
 constexpr int kRingRowsTotal = kRingRows * kRingSlots;     // 16: ring row = relative row & 15
@@ -49,7 +51,7 @@ struct Ring {
     static constexpr unsigned Bytes = unsigned(Chunk) * 4u;
     // ring slots, then one 13-float row per thread for the edge gathers
     static constexpr int Smem = kRingSlots * int(Bytes) + Threads * Q * 4;
-    static constexpr int BlocksPerSm = W == 64 ? 2 : 4;
+    static constexpr int BlocksPerSm = W == 64 ? 2 : 5;
     static_assert(Bytes % 128 == 0, "ring slots are tensor-copy destinations: 128-byte aligned");
     // nodes of one edge work item: one per thread of the block
     static constexpr int EdgeNodes = Threads;
@@ -63,30 +65,6 @@ __host__ __device__ inline long long ring_edge_count(int nx, int ny)
 {
     return 4LL * nx + 4LL * (ny > 4 ? ny - 4 : 0);
 }
-
-// Paired steps (pair_step_kernel, lbm13_step2.cu): two time steps of a
-// lattice periodic in x and y per launch.  Persistent blocks, one per SM,
-// take output tiles of kPairX x kPairY nodes in turn.  For each tile the rows
-// and columns within four links of it (kPairInX x kPairInY nodes, all 13
-// planes, [row][plane][column]) arrive in shared memory (a tensor copy issued
-// while the previous tile is stepped: two input buffers), the kPairMidX x
-// kPairMidY nodes within two links are stepped into a third tile, and the
-// output tile is stepped from that and written to the other buffer: one read
-// and one write of every population per two updates.  The intermediate tile
-// is one warp wide (every warp steps whole rows of 32 nodes), the output
-// tile 28 columns of it.
-constexpr int kPairX = 28, kPairY = 28;
-constexpr int kPairInX = kPairX + 8, kPairInY = kPairY + 8;
-constexpr int kPairMidX = kPairX + 4, kPairMidY = kPairY + 4;
-constexpr int kPairIn = kPairInY * Q * kPairInX;     // floats of one input box
-constexpr int kPairInStride = (kPairIn + 31) / 32 * 32;  // input buffers 128 bytes apart
-constexpr int kPairMid = kPairMidY * Q * kPairMidX;  // floats
-constexpr int kPairThreads = 512;
-constexpr int kPairBlocksPerSm = 1;
-constexpr int kPairSmem = (2 * kPairInStride + kPairMid) * 4;  // 187,776 bytes: one block per SM
-static_assert(kPairMidX == 32, "the intermediate tile is one warp wide");
-// a tensor copy's shared-memory destination must be 128-byte aligned
-static_assert(kPairInStride * 4 % 128 == 0, "paired-step input buffers 128-byte aligned");
 
 // One lattice's tensor maps: map[p] describes the buffer read when the step's
 // parity is p, as a 3-D tensor (x: nx, y: ny, plane: 13) with row stride
@@ -112,17 +90,6 @@ struct LatticeMaps {
 cudaError_t launch_batch_tma(const BatchDesc<float, float> *descs, const LatticeMaps *maps, const int2 *work,
                              int ntiles, int parity, int groups, unsigned *err, cudaStream_t s, int issue = 1,
                              unsigned long long wait_ns = 1000000000ull);
-
-// Paired steps of one FP32 lattice periodic in x and y: reads a.fin, writes
-// the state two steps later to a.fout.  map describes a.fin as (x: nx, plane:
-// 13, y: ny) in boxes of kPairInX x 13 x kPairInY; tiles clear of the periodic
-// seam load through it, the others by wrapped global loads.  Every tensor
-// copy's wait is bounded by wait_ns of the global timer; after a timeout the
-// block sets *err, waits (bounded) for its copies in flight and leaves without
-// writing the tile (issue = 0 withholds the copies: the self-check of that
-// wait).
-cudaError_t launch_pair_step(const StepArgs<float, float> &a, const CUtensorMap &map, bool force, unsigned *err,
-                             cudaStream_t s, int issue = 1, unsigned long long wait_ns = 1000000000ull);
 
 // Ring-staged batched step (FP32): one block per work item (lattice, strip of
 // `width` = 64 or 32 columns x groups 4-row groups), packed as

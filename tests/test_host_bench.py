@@ -65,4 +65,8 @@ def test_paired_kernel_records_follow_their_own_sources():
     ipl = bench.pair_record("pair_fp32_warp_instr_per_lu")
     assert ipl is None or 5.0 < ipl < 20.0
     traffic = bench.pair_record("pair_fp32_8192")
-    assert traffic is None or traffic > 52 * 2 * 8192 * 8192  # at least the algorithmic bytes of a paired launch
+    # near the algorithmic bytes of a paired launch (52 per update, two steps): a
+    # little under them when written lines are still in L2 at the launch's end,
+    # well over them only if tiles re-read their input
+    algorithmic = 52 * 2 * 8192 * 8192
+    assert traffic is None or 0.9 * algorithmic < traffic < 1.2 * algorithmic
