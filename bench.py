@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--batched-config", default="",
                     help="R,BY,ctas_per_sm,order for the batched plan instead of autotuning")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-pairs", action="store_true",
+                    help="one time step per launch on the main lattice (the single-step kernel)")
     return ap.parse_args()
 
 
@@ -433,6 +435,8 @@ def run_ours(args):
                 torch.full((n, n), T0, device=dev, dtype=torch.float64))
 
     lat = lbm13.Lattice(n, n, p, W.boundary(), precision=prec)
+    if args.no_pairs:
+        lat.set_pair_steps(lbm13.PAIR_OFF)
     f = device_fields()
     lat.set_state_device(*f)
     del f

@@ -173,7 +173,11 @@ LBM13_HD float recip(float x) { return 1.0f / x; }
 // 1/rho for the collision, where it only scales second-order terms (the
 // momentum-flux equilibria j_x^2 - j_y^2 and j_x j_y, the force's work): one
 // Newton step after the FP32 seed leaves a relative error near 2^-47, i.e.
-// below 1e-18 in those terms at |u| ~ 0.01.
+// below 1e-18 in those terms at |u| ~ 0.01.  FP32 takes CUDA's fast division
+// (__fdividef, within 2 ulp for divisors in [2^-126, 2^126]): a relative
+// error of about 2.4e-7 in terms no larger than the deviations they are added
+// to, i.e. at the level of those deviations' own FP32 rounding; every kernel
+// rounds it the same way.
 LBM13_HD double recip_uu(double x)
 {
 #ifdef __CUDA_ARCH__
@@ -183,7 +187,14 @@ LBM13_HD double recip_uu(double x)
     return 1.0 / x;
 #endif
 }
-LBM13_HD float recip_uu(float x) { return 1.0f / x; }
+LBM13_HD float recip_uu(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.0f, x);
+#else
+    return 1.0f / x;
+#endif
+}
 
 // Explicitly rounded products for the collision.  Every product in collide
 // is written as rn_mul (never merged with an addition) or rn_fma (one
