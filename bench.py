@@ -128,16 +128,43 @@ STEP_SOURCES = ("lbm13_internal.h", "lbm13_math.cuh", "lbm13_stepdev.cuh", "lbm1
 PAIR_SOURCES = STEP_SOURCES + ("lbm13_pair.h", "lbm13_mbar.cuh", "lbm13_step2.cu")
 
 
+def code_only(text):
+    """C/C++ source without its comments and blank lines, trailing blanks
+    dropped (string and character literals are kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_hash(sources=STEP_SOURCES):
-    """Hash of the sources that define a kernel (its launch, body and
-    arguments; the single-step kernel by default, PAIR_SOURCES for the paired
-    one): a profile record only applies to the kernel it was taken on."""
+    """Hash of the code of the sources that define a kernel (its launch, body
+    and arguments; the single-step kernel by default, PAIR_SOURCES for the
+    paired one), comments left out: a profile record only applies to the
+    kernel it was taken on, whatever its comments say since."""
     import hashlib
     src = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
     h = hashlib.sha256()
     for name in sources:
-        with open(os.path.join(src, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(src, name), encoding="utf-8") as f:
+            h.update(code_only(f.read()).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

@@ -26,7 +26,7 @@ constexpr int kPairInStride = (kPairIn + 31) / 32 * 32;  // input buffers 128 by
 constexpr int kPairMid = kPairMidY * Q * kPairMidX;  // floats
 constexpr int kPairThreads = 512;
 constexpr int kPairBlocksPerSm = 1;
-constexpr int kPairSmem = (2 * kPairInStride + kPairMid) * 4;  // 187,776 bytes: one block per SM
+constexpr int kPairSmem = (2 * kPairInStride + kPairMid) * 4;  // 188,160 bytes: one block per SM
 static_assert(kPairMidX == 32, "the intermediate tile is one warp wide");
 // a tensor copy's shared-memory destination must be 128-byte aligned
 static_assert(kPairInStride * 4 % 128 == 0, "paired-step input buffers 128-byte aligned");
