@@ -55,15 +55,20 @@
  *      E* gains 26 q; like the force it is split about the collision: the
  *      equilibria are taken at E + 13 q and the temperature read-out is
  *      half-way through the step, T = (p* - q/2) / rho.
- *   corners: a diagonal that crosses two walls at once bounces back with the
- *      mean of the two walls' data.
+ *   corners: a diagonal that crosses two walls at once bounces back to its
+ *      own node and takes the R14 correction of each wall it crosses, each at
+ *      that wall's own data at the node.  The two single-wall diagonals of
+ *      the same node take those same corrections with the other sign of the
+ *      tangential component, so the node's wall corrections carry no net mass
+ *      (as on a flat wall) and a closed bounce-back box keeps its mass
+ *      whatever its walls' speeds (a correction at the mean of the two walls'
+ *      data does not: it moves mass between the corners of a moving wall).
  *
- * Parity unpinned: two sub-choices above pass every pin of the test suite
- * when replaced by a plausible alternative (the mutation tests plant each
- * alternative in a copy of this file): the half-force shift of R9 (equilibria
- * at j instead of j + F/2 move only non-conserved moments by O(F)) and the
- * corner mean (one wall's density instead changes one link of the four corner
- * nodes).  Nothing the paper prints fixes either.
+ * Parity unpinned: one sub-choice above passes every pin of the test suite
+ * when replaced by a plausible alternative (the mutation tests plant it in a
+ * copy of this file): the half-force shift of R9 (equilibria at j instead of
+ * j + F/2 move only non-conserved moments by O(F)).  Nothing the paper prints
+ * fixes it.
  *
  * Storage: post-collision distributions f*(t), plane-major f[j][y][x], FP64.
  */
@@ -393,15 +398,11 @@ static int stream(orc_lattice *L)
                 }
                 int jb = opposite(j);
                 if (out_x && out_y) {
-                    /* corner diagonal: lands on x_f, bounce-back with the mean
-                     * of the two walls' data */
+                    /* corner diagonal: lands on x_f, bounce-back with the
+                     * correction of each wall it crosses */
                     int sx = tx < 0 ? 0 : 1, sy = ty < 0 ? 2 : 3;
-                    wall_state a = wall_data(L, fs, sx, y), b = wall_data(L, fs, sy, x), c;
-                    c.rho = 0.5 * (a.rho + b.rho);
-                    c.E = 0.5 * (a.E + b.E);
-                    c.ux = 0.5 * (a.ux + b.ux);
-                    c.uy = 0.5 * (a.uy + b.uy);
-                    g[jb * plane + (size_t)y * nx + x] = val - 2.0 * feq_part(L, &c, j, 1);
+                    wall_state a = wall_data(L, fs, sx, y), b = wall_data(L, fs, sy, x);
+                    g[jb * plane + (size_t)y * nx + x] = val - 2.0 * feq_part(L, &a, j, 1) - 2.0 * feq_part(L, &b, j, 1);
                     continue;
                 }
                 /* one wall: side, coordinate along it, and the landing node

@@ -35,7 +35,6 @@ struct lbm13_lattice {
     Coef<float> kf{};
     WallArgs<double> wd[4]{};
     WallArgs<float> wf[4]{};
-    double corner_poly[4][5] = {};  // corner corrections as polynomials (StepArgs::corner_poly)
     bool force = false;
     // CUDA graphs of kGraphSteps steps, one per starting buffer parity
     cudaStream_t cap_stream = nullptr;
@@ -296,13 +295,10 @@ template <typename C>
 void fill_walls(lbm13_t h, WallArgs<C> *w)
 {
     const lbm13_wall *src[4] = {&h->b.west, &h->b.east, &h->b.south, &h->b.north};
-    double U[4][2];
     for (int s = 0; s < 4; ++s) {
         const lbm13_wall &in = *src[s];
         WallArgs<C> &o = w[s];
         const double ux = s <= EAST ? 0.0 : in.u_t, uy = s <= EAST ? in.u_t : 0.0;
-        U[s][0] = ux;
-        U[s][1] = uy;
         o.kind = in.kind;
         o.needs_data = in.kind == WALL_MIXED || (in.kind == WALL_BB && in.u_t != 0.0);
         o.ux = C(ux);
@@ -334,19 +330,8 @@ void fill_walls(lbm13_t h, WallArgs<C> *w)
             for (int m = 0; m < 5; ++m) o.poly[i][m] = C(a[m]);
         }
     }
-    // corners: bounce-back with the mean of the two walls' states
-    for (int c = 0; c < 4; ++c) {
-        const int sx = (c & 1) ? EAST : WEST, sy = (c & 2) ? NORTH : SOUTH;
-        const double ux = 0.5 * (U[sx][0] + U[sy][0]), uy = 0.5 * (U[sx][1] + U[sy][1]);
-        const int j = corner_link(c), jn = copp(j);
-        quadratic_coefficients(
-            [&](double dr, double de) {
-                double f[Q];
-                wall_equilibrium(h, dr, de, ux, uy, f);
-                return f[j] - f[jn];
-            },
-            h->corner_poly[c]);
-    }
+    // a corner diagonal crosses both walls and takes both walls' corrections
+    // for its link (their slots above), each at its own wall's state
 }
 
 template <typename T>
@@ -427,8 +412,6 @@ StepArgs<T, C> step_args(lbm13_t h, int cur, const Coef<C> &k, const WallArgs<C>
     a.bad = h->bad;
 #endif
     for (int s = 0; s < 4; ++s) a.wall[s] = w[s];
-    for (int c = 0; c < 4; ++c)
-        for (int m = 0; m < 5; ++m) a.corner_poly[c][m] = C(h->corner_poly[c][m]);
     return a;
 }
 

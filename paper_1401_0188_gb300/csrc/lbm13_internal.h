@@ -49,17 +49,11 @@ LBM13_HD constexpr int wall_slot(int side, int j)
     return wall_link(side, 0) == j ? 0 : wall_link(side, 1) == j ? 1 : wall_link(side, 2) == j ? 2
          : wall_link(side, 3) == j ? 3 : -1;
 }
-// The diagonal entering the lattice at each corner: 0 (x=0, y=0) j=5,
-// 1 (x=nx-1, y=0) j=6, 2 (x=0, y=ny-1) j=8, 3 (x=nx-1, y=ny-1) j=7.
-LBM13_HD constexpr int corner_link(int c) { return c == 0 ? 5 : c == 1 ? 6 : c == 2 ? 8 : 7; }
 
 template <typename T, typename C>
 struct alignas(16) StepArgs {
     const T *__restrict__ fin;
     T *__restrict__ fout;
-    // corner c's bounce-back correction as a polynomial in the mean of the two
-    // walls' (drho, dE), with the mean wall velocity (same form as WallArgs::poly)
-    C corner_poly[4][5];
     int nx, ny;
     int per_x, per_y;
     long long pitch;  // elements per row

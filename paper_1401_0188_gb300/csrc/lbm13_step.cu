@@ -27,7 +27,7 @@
 // makes the wall's net normal mass flux zero), u_w the wall velocity, and E_w from the wall
 // temperature, E_w = rho_w (26 T_w - 28) + 13 rho_w |u_w|^2, or extrapolated
 // like rho_w at an adiabatic wall.  A diagonal that crosses two walls at a
-// corner bounces back with the mean of the two walls' states.  The nodes next
+// corner bounces back with each wall's correction at that wall's own state.  The nodes next
 // to a wall evaluate its state at their own position and add the wall
 // correction, a quadratic in (rho_w, E_w) whose coefficients the host computes
 // once per lattice.

@@ -198,13 +198,12 @@ __device__ __forceinline__ void gather_body(const StepArgs<T, C> &a, int x, int 
     const bool nd_x = a.wall[sx_side].needs_data != 0, nd_y = a.wall[sy_side].needs_data != 0;
     // the wall states at this node's position, before the pulls so that
     // they are not live across the calls: a wall's own state where it needs
-    // data; at a corner node (the only one whose diagonal crosses both walls)
-    // both states enter the corner's correction when either wall needs data
+    // data (a corner node's diagonal takes each crossed wall's correction at
+    // that wall's own state, so no other state is needed)
     const bool near_x = !px && (x <= 1 || x >= nx - 2), near_y = !py && (y <= 1 || y >= ny - 2);
-    const bool corner_node = !px && !py && (x == 0 || x == nx - 1) && (y == 0 || y == ny - 1);
     WallState<C> stx = {C(0), C(0)}, sty = {C(0), C(0)};
-    if (near_x && (nd_x || (corner_node && nd_y))) stx = wall_state_of(a, sx_side, y, src);
-    if (near_y && (nd_y || (corner_node && nd_x))) sty = wall_state_of(a, sy_side, x, src);
+    if (near_x && nd_x) stx = wall_state_of(a, sx_side, y, src);
+    if (near_y && nd_y) sty = wall_state_of(a, sy_side, x, src);
     C v[Q];
     unsigned cross = 0u, neg = 0u, crx = 0u, cry = 0u;
 #pragma unroll
@@ -227,20 +226,16 @@ __device__ __forceinline__ void gather_body(const StepArgs<T, C> &a, int x, int 
         crx |= (ox ? 1u : 0u) << j;
         cry |= (oy ? 1u : 0u) << j;
     }
-    const int corner = (west ? 0 : 1) + (south ? 0 : 2);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const bool ox = (crx >> j) & 1u, oy = (cry >> j) & 1u;
+        // the correction of each wall the link crosses, at that wall's state:
+        // a corner diagonal crosses both and takes both (with the node's two
+        // single-wall diagonals they carry no net mass, as on a flat wall)
         C ad = C(0);
-        if (ox && oy) {
-            if (nd_x || nd_y)
-                ad = wall_poly(a.corner_poly[corner], C(0.5) * (stx.rho + sty.rho), C(0.5) * (stx.E + sty.E));
-        } else if (ox) {
-            if (nd_x) ad = wall_poly(a.wall[sx_side].poly[west ? wall_slot(WEST, j) : wall_slot(EAST, j)], stx.rho, stx.E);
-        } else if (oy) {
-            if (nd_y)
-                ad = wall_poly(a.wall[sy_side].poly[south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j)], sty.rho, sty.E);
-        }
+        if (ox && nd_x) ad = wall_poly(a.wall[sx_side].poly[west ? wall_slot(WEST, j) : wall_slot(EAST, j)], stx.rho, stx.E);
+        if (oy && nd_y)
+            ad += wall_poly(a.wall[sy_side].poly[south ? wall_slot(SOUTH, j) : wall_slot(NORTH, j)], sty.rho, sty.E);
         const C w = ((neg >> j) & 1u) ? -v[j] : v[j];
         f[j] = ((cross >> j) & 1u) ? w + ad : v[j];
     }

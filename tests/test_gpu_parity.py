@@ -96,8 +96,6 @@ def _cases(T0):
         "cavity": (48, 40, W.cavity(T0, 0.01, 2e-4)),
         "couette": (37, 30, W.couette(T0, 0.05, 0.01)),
         "poiseuille": (40, 33, W.poiseuille(1e-5)),
-        # moving walls stay inside the scheme's stability envelope (a 0.05 lid on
-        # 36 x 36 diverges after ~400 steps in the oracle and on the GPU alike)
         "lid_driven": (36, 36, W.boundary(west=W.wall(B), east=W.wall(B), south=W.wall(B),
                                           north=W.wall(B, 0.03))),
         "all_mixed_moving": (34, 29, W.boundary(west=W.wall(M, -0.01, hot), east=W.wall(M, 0.015, cold),
@@ -152,6 +150,30 @@ def test_walls_from_fields_fp64(L, pstar, case):
     o.step(200)
     g.step(200)
     assert _maxdiff(o.moments(), g.moments()) <= TOL64
+
+
+@pytest.mark.parametrize("U", [0.03, 0.05])
+def test_lid_driven_box_keeps_its_mass_fp64(L, pstar, U):
+    """A closed bounce-back box under a moving lid (R14, Sec. 7), 36 x 36 from
+    rest, 2000 steps: the moments match the oracle within 1e-10 and the total
+    mass stays at its initial value to round-off.  Each corner diagonal takes
+    the correction of both walls it crosses at their own states, so the
+    corners, like every flat-wall node, add no mass (a correction at the mean
+    of the two walls' states moved O(U) of mass per step between the lid's
+    corners)."""
+    T0 = _T0(pstar)
+    B = W.WALL_BB
+    bnd = W.boundary(west=W.wall(B), east=W.wall(B), south=W.wall(B), north=W.wall(B, U))
+    o, g = _pair(L, 36, 36, pstar, bnd)
+    _init_fields(o, g, (1.0, 0.0, 0.0, T0))
+    m0 = g.residual()[4]
+    o.step(2000)
+    g.step(2000)
+    assert _maxdiff(o.moments(), g.moments()) <= TOL64
+    r = g.residual()
+    assert m0 == pytest.approx(36 * 36, abs=1e-9)
+    assert abs(r[4] - m0) < 1e-9, r[4] - m0
+    assert np.abs(g.macro()[1]).max() > 0.5 * U  # the lid drives the flow
 
 
 # --------------------------------------------------------------- read-outs

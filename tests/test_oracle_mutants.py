@@ -3,12 +3,10 @@ in a copy of lbm13_oracle.c (a flipped sign, a dropped term, a transposed
 operand, a wrong index or rate), builds it on the CPU, and runs the oracle's
 pin tests against that build; at least one pin must fail.
 
-Two plausible mistakes are known to pass every pin and are not listed:
+One plausible mistake is known to pass every pin and is not listed:
 evaluating the equilibria at j instead of j + F/2 (reading R9: it moves only
-the non-conserved moments by O(F), below every pin's tolerance) and giving a
-corner diagonal one wall's density instead of the two walls' mean (it changes
-one link of the four corner nodes).  The GPU path is held to the oracle on
-both by the parity tests."""
+the non-conserved moments by O(F), below every pin's tolerance).  The GPU path
+is held to the oracle on it by the parity tests."""
 import os
 import shutil
 import subprocess
@@ -50,6 +48,11 @@ MUTANTS = {
     "wall_energy_drops_kinetic_part": ("s.E = s.rho * (26.0 * w->T - 28.0) + 13.0 * s.rho * (s.ux * s.ux + s.uy * s.uy);",
                                        "s.E = s.rho * (26.0 * w->T - 28.0);"),
     "nusselt_kappa_inverted": ("double kappa = L->p.nu / L->p.Pr;", "double kappa = L->p.nu * L->p.Pr;"),
+    "corner_at_mean_wall_data": ("val - 2.0 * feq_part(L, &a, j, 1) - 2.0 * feq_part(L, &b, j, 1);",
+                                 "val - 2.0 * feq_part(L, &(wall_state){0.5 * (a.rho + b.rho), "
+                                 "0.5 * (a.E + b.E), 0.5 * (a.ux + b.ux), 0.5 * (a.uy + b.uy)}, j, 1);"),
+    "corner_one_wall_only": ("val - 2.0 * feq_part(L, &a, j, 1) - 2.0 * feq_part(L, &b, j, 1);",
+                             "val - 2.0 * feq_part(L, &b, j, 1);"),
 }
 
 
