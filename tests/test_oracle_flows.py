@@ -136,6 +136,29 @@ def test_closed_box_with_moving_walls_conserves_mass(pstar, case):
     assert np.abs(m[4]).max() > 1e-3  # the walls drive a flow
 
 
+@pytest.mark.parametrize("case", ["bb", "mixed", "mixed_zero_flux", "x_walls_mixed"])
+def test_fluid_translating_with_its_walls_is_a_fixed_point(pstar, case):
+    """Galilean consistency of the wall rules (R10, R11, R14, Sec. 7): when a
+    channel's walls both move at U and a temperature wall is at the fluid's
+    temperature, the equilibrium translating at U is an exact steady state, so
+    every bounce-back and anti-bounce-back link must hand back the populations
+    that the translating equilibrium has there (the wall energy includes its
+    kinetic part 13 rho |u_w|^2)."""
+    T0 = _T0(pstar)
+    B, M = O.WALL_BB, O.WALL_MIXED
+    U = 0.03
+    b = {"bb": O.boundary(south=O.wall(B, U), north=O.wall(B, U)),
+         "mixed": O.boundary(south=O.wall(M, U, T0), north=O.wall(M, U, T0)),
+         "mixed_zero_flux": O.boundary(south=O.wall(M, U, T0), north=O.wall(M, U, T0), wall_density=1),
+         "x_walls_mixed": O.boundary(west=O.wall(M, U, T0), east=O.wall(M, U, T0))}[case]
+    lat = O.Lattice(16, 12, pstar, b)
+    ux, uy = (0.0, U) if case == "x_walls_mixed" else (U, 0.0)
+    lat.set_equilibrium(1.0, ux, uy, T0)
+    f0 = lat.get_raw()
+    lat.step(100)
+    assert np.abs(lat.get_raw() - f0).max() < 1e-13
+
+
 def test_periodic_momentum_budget_under_force(pstar):
     """Periodic lattice, buoyancy F = (rho - 1) g: sum j grows by sum F per step."""
     n = 16
