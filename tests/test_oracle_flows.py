@@ -204,6 +204,49 @@ def test_step_commutes_with_mirror_images(pstar, axis):
     assert np.abs(flip(mir.get_raw()[perm]) - a).max() < 1e-13
 
 
+# velocity index j -> index of v_j turned by a quarter turn, (vx, vy) -> (-vy, vx)
+_QUARTER = [0, 2, 3, 4, 1, 6, 7, 8, 5, 10, 11, 12, 9]
+
+
+def test_step_commutes_with_a_quarter_turn(pstar):
+    """The velocity set is symmetric under a quarter turn and the x-wall and
+    y-wall rules are the same rule (Sec. 2, Sec. 7): stepping a square lattice
+    turned by 90 degrees (populations turned, each wall moved to the side it
+    turns into with its tangential speed carried along, force turned) gives
+    the turned image of the stepped lattice."""
+    T0 = _T0(pstar)
+    B, M = O.WALL_BB, O.WALL_MIXED
+    vx, vy = O.velocities()
+    assert all((vx[_QUARTER[j]], vy[_QUARTER[j]]) == (-vy[j], vx[j]) for j in range(13))
+    n = 12
+    west, east = O.wall(M, 0.01, T0 + 0.004), O.wall(M, -0.015, T0 - 0.003)
+    south, north = O.wall(B, 0.02), O.wall(M, -0.01, T0 + 0.002)
+    g, heat = (3e-5, -2e-5), 1e-6
+    neg = lambda d: dict(d, u_t=-d["u_t"])
+    lat = O.Lattice(n, n, pstar, O.boundary(west=west, east=east, south=south, north=north, gx=g[0], gy=g[1],
+                                            rho_ref=1.0, wall_density=1, heat=heat))
+    # (x, y) -> (n-1-y, x): west -> south, east -> north, south -> east, north -> west;
+    # +y (x-wall speeds) turns into -x, +x (y-wall speeds) into +y
+    turned = O.Lattice(n, n, pstar, O.boundary(south=neg(west), north=neg(east), east=south, west=north,
+                                               gx=-g[1], gy=g[0], rho_ref=1.0, wall_density=1, heat=heat))
+
+    def turn(f):
+        out = np.empty_like(f)
+        for j in range(13):
+            out[_QUARTER[j]] = f[j][::-1].T
+        return out
+
+    w = lat.constants()["w"]
+    f = w[:, None, None] * (1 + 1e-2 * np.random.default_rng(3).standard_normal((13, n, n)))
+    lat.set_raw(f)
+    turned.set_raw(turn(f))
+    lat.step(200)
+    turned.step(200)
+    a = lat.get_raw()
+    assert np.abs(a - w[:, None, None]).max() > 1e-3
+    assert np.abs(turn(a) - turned.get_raw()).max() < 1e-13
+
+
 def test_periodic_momentum_budget_under_force(pstar):
     """Periodic lattice, buoyancy F = (rho - 1) g: sum j grows by sum F per step."""
     n = 16
