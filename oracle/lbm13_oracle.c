@@ -64,11 +64,13 @@
  *      whatever its walls' speeds (a correction at the mean of the two walls'
  *      data does not: it moves mass between the corners of a moving wall).
  *
- * Parity unpinned: one sub-choice above passes every pin of the test suite
- * when replaced by a plausible alternative (the mutation tests plant it in a
- * copy of this file): the half-force shift of R9 (equilibria at j instead of
- * j + F/2 move only non-conserved moments by O(F)).  Nothing the paper prints
- * fixes it.
+ * Parity unpinned: two sub-choices above pass every pin of the test suite
+ * when replaced by a plausible alternative: the half-force shift of R9
+ * (equilibria at j instead of j + F/2 move only non-conserved moments by
+ * O(F)), and the linear coefficients of R12 (a quadratic extrapolation through
+ * the first three nodes, 15/8, -10/8, 3/8, changes the wall density at second
+ * order in the node spacing; the pins exclude only no extrapolation at all).
+ * Nothing the paper prints fixes either.
  *
  * Storage: post-collision distributions f*(t), plane-major f[j][y][x], FP64.
  */

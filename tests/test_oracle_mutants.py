@@ -3,10 +3,12 @@ in a copy of lbm13_oracle.c (a flipped sign, a dropped term, a transposed
 operand, a wrong index or rate), builds it on the CPU, and runs the oracle's
 pin tests against that build; at least one pin must fail.
 
-One plausible mistake is known to pass every pin and is not listed:
+Two plausible alternatives are known to pass every pin and are not listed:
 evaluating the equilibria at j instead of j + F/2 (reading R9: it moves only
-the non-conserved moments by O(F), below every pin's tolerance).  The GPU path
-is held to the oracle on it by the parity tests."""
+the non-conserved moments by O(F), below every pin's tolerance), and a
+quadratic instead of a linear extrapolation of the wall density (reading R12:
+a change at second order in the node spacing).  The GPU path is held to the
+oracle on both by the parity tests."""
 import os
 import shutil
 import subprocess
