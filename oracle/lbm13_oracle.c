@@ -67,9 +67,10 @@
  * Parity unpinned: two sub-choices above pass every pin of the test suite
  * when replaced by a plausible alternative: the half-force shift of R9
  * (equilibria at j instead of j + F/2 move only non-conserved moments by
- * O(F)), and the linear coefficients of R12 (a quadratic extrapolation through
- * the first three nodes, 15/8, -10/8, 3/8, changes the wall density at second
- * order in the node spacing; the pins exclude only no extrapolation at all).
+ * O(F)), and the linear coefficients of R12, also used for E_w at moving
+ * adiabatic walls (a quadratic extrapolation through the first three nodes,
+ * 15/8, -10/8, 3/8, changes the wall state at second order in the node
+ * spacing; the pins exclude only no extrapolation at all).
  * Nothing the paper prints fixes either.
  *
  * Storage: post-collision distributions f*(t), plane-major f[j][y][x], FP64.
