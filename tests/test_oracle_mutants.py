@@ -55,6 +55,10 @@ MUTANTS = {
                                  "0.5 * (a.E + b.E), 0.5 * (a.ux + b.ux), 0.5 * (a.uy + b.uy)}, j, 1);"),
     "corner_one_wall_only": ("val - 2.0 * feq_part(L, &a, j, 1) - 2.0 * feq_part(L, &b, j, 1);",
                              "val - 2.0 * feq_part(L, &b, j, 1);"),
+    "north_wall_second_node_misplaced": ("else                { y0 = L->ny - 1;  y1 = L->ny - 2;  x0 = x1 = pos; }",
+                                         "else                { y0 = L->ny - 1;  y1 = L->ny - 3;  x0 = x1 = pos; }"),
+    "east_corners_take_west_wall_data": ("int sx = tx < 0 ? 0 : 1, sy = ty < 0 ? 2 : 3;",
+                                         "int sx = 0, sy = ty < 0 ? 2 : 3;"),
 }
 
 
