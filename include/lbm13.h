@@ -88,7 +88,11 @@ typedef enum {
 /* A wall lies half a link outside the first/last node.  u_t is its velocity
  * along the wall (+x for south/north walls, +y for west/east walls); T is its
  * temperature (used by LBM13_WALL_MIXED only).  The wall density is the
- * linear extrapolation 1.5 rho(first node) - 0.5 rho(second node). */
+ * linear extrapolation 1.5 rho(first node) - 0.5 rho(second node).  Where two
+ * walls meet (the paper gives no corner rule), the diagonal that leaves a
+ * corner node across both bounces back with the moving-wall correction of
+ * each wall, at that wall's own state; a closed box then keeps its mass
+ * whatever its walls' speeds (with bounce-back walls, its energy too). */
 typedef struct {
     int kind;   /* lbm13_wall_kind */
     double u_t;
