@@ -1,0 +1,105 @@
+"""The kernels' per-node basis code on the host, without a GPU: the velocity
+tables and the factorised moment transforms of csrc/lbm13_math.cuh (host and
+device functions, which the library's host code also uses) are compiled with
+the host compiler and checked against the paper's velocity set
+(tests/golden/velocities.txt, Sec. 1 and Sec. 2) and the oracle's dense moment
+matrix M of Eq. (d2q13-polynomes) and its inverse M^T D^-1.
+
+This checks the source of the transforms the step kernels run (pair sums and
+differences instead of 2 x 169 products); the GPU parity tests check the
+compiled kernels end to end."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1401_0188_gb300", "csrc")
+CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+Q = 13
+FIELDS = ("rho", "E", "eps", "vpi", "jx", "jy", "qx", "qy", "rx", "ry", "XX", "XY", "XXe")
+
+SRC = r"""
+#include "lbm13_math.cuh"
+using namespace lbm13;
+extern "C" void tables(int *vx, int *vy, int *opp)
+{
+    for (int j = 0; j < Q; ++j) { vx[j] = cvx(j); vy[j] = cvy(j); opp[j] = copp(j); }
+}
+extern "C" void forward_moments(const double *f, double *m)
+{
+    Mom<double> r;
+    forward(f, r);
+    const double v[Q] = {r.rho, r.E, r.eps, r.vpi, r.jx, r.jy, r.qx, r.qy, r.rx, r.ry, r.XX, r.XY, r.XXe};
+    for (int k = 0; k < Q; ++k) m[k] = v[k];
+}
+extern "C" void inverse_populations(const double *d, int with_rho, double *f)
+{
+    const Mom<double> r = {d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8], d[9], d[10], d[11], d[12]};
+    for (int j = 0; j < Q; ++j) f[j] = 0.0;
+    if (with_rho) inverse_add<true>(r, f);
+    else inverse_add<false>(r, f);
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    if shutil.which("g++") is None or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    d = tmp_path_factory.mktemp("hostmath")
+    src, so = d / "host_math.cpp", d / "host_math.so"
+    src.write_text(SRC)
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-w", "-I", CSRC, "-I", CUDA_INC,
+                           str(src), "-o", str(so)])
+    L = C.CDLL(str(so))
+    ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    L.tables.argtypes = [ip, ip, ip]
+    L.forward_moments.argtypes = [dp, dp]
+    L.inverse_populations.argtypes = [dp, C.c_int, dp]
+    return L
+
+
+def _golden_velocities():
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "velocities.txt"))
+            if l.strip() and not l.startswith("#")]
+    return np.array([[int(r[1]), int(r[2])] for r in rows])
+
+
+def test_velocity_tables_follow_the_paper(lib):
+    vx, vy, opp = (np.zeros(Q, dtype=np.int32) for _ in range(3))
+    lib.tables(vx, vy, opp)
+    v = _golden_velocities()
+    assert np.array_equal(vx, v[:, 0]) and np.array_equal(vy, v[:, 1])
+    assert np.array_equal(vx[opp], -vx) and np.array_equal(vy[opp], -vy)
+
+
+def test_factorised_forward_transform_is_M(lib):
+    M, _, _ = O.basis()
+    f = np.random.default_rng(11).standard_normal((64, Q))
+    for row in f:
+        m = np.zeros(Q)
+        lib.forward_moments(np.ascontiguousarray(row), m)
+        assert np.allclose(m, M @ row, rtol=0, atol=1e-12), dict(zip(FIELDS, m - M @ row))
+
+
+@pytest.mark.parametrize("with_rho", [1, 0])
+def test_factorised_inverse_is_M_transposed_over_D(lib, with_rho):
+    """inverse_add adds sum_k M_kj d_k for increments d_k already divided by
+    D_k, so forward(inverse(m / D)) returns m; without the rho row the density
+    increment is left out (the collision never changes rho)."""
+    M, D, Minv = O.basis()
+    m = np.random.default_rng(12).standard_normal((64, Q))
+    for row in m:
+        f = np.zeros(Q)
+        lib.inverse_populations(np.ascontiguousarray(row / D), with_rho, f)
+        want = M.T @ (row / D) if with_rho else M.T @ (row / D) - M[0] * row[0] / D[0]
+        assert np.allclose(f, want, rtol=0, atol=1e-12)
+        if with_rho:
+            assert np.allclose(f, Minv @ row, rtol=0, atol=1e-12)
