@@ -38,6 +38,11 @@ extern "C" void forward_moments(const double *f, double *m)
     const double v[Q] = {r.rho, r.E, r.eps, r.vpi, r.jx, r.jy, r.qx, r.qy, r.rx, r.ry, r.XX, r.XY, r.XXe};
     for (int k = 0; k < Q; ++k) m[k] = v[k];
 }
+extern "C" void wall_moments(const double *f, double *out)
+{
+    out[0] = mass_dev(f);
+    out[1] = energy_dev(f);
+}
 extern "C" void inverse_populations(const double *d, int with_rho, double *f)
 {
     const Mom<double> r = {d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8], d[9], d[10], d[11], d[12]};
@@ -63,6 +68,7 @@ def lib(tmp_path_factory):
     L.tables.argtypes = [ip, ip, ip]
     L.forward_moments.argtypes = [dp, dp]
     L.inverse_populations.argtypes = [dp, C.c_int, dp]
+    L.wall_moments.argtypes = [dp, dp]
     return L
 
 
@@ -103,3 +109,13 @@ def test_factorised_inverse_is_M_transposed_over_D(lib, with_rho):
         assert np.allclose(f, want, rtol=0, atol=1e-12)
         if with_rho:
             assert np.allclose(f, Minv @ row, rtol=0, atol=1e-12)
+
+
+def test_wall_state_moments_are_the_rho_and_E_rows(lib):
+    """The two moments a wall state is extrapolated from (Sec. 7) are the rho
+    and E rows of M."""
+    M, _, _ = O.basis()
+    for row in np.random.default_rng(13).standard_normal((32, Q)):
+        out = np.zeros(2)
+        lib.wall_moments(np.ascontiguousarray(row), out)
+        assert np.allclose(out, M[:2] @ row, rtol=0, atol=1e-12)
