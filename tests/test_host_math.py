@@ -25,8 +25,15 @@ Q = 13
 FIELDS = ("rho", "E", "eps", "vpi", "jx", "jy", "qx", "qy", "rx", "ry", "XX", "XY", "XXe")
 
 SRC = r"""
-#include "lbm13_math.cuh"
+#include "lbm13_internal.h"
 using namespace lbm13;
+extern "C" void wall_tables(int *link, int *slot)
+{
+    for (int s = 0; s < 4; ++s) {
+        for (int i = 0; i < 4; ++i) link[4 * s + i] = wall_link(s, i);
+        for (int j = 0; j < Q; ++j) slot[Q * s + j] = wall_slot(s, j);
+    }
+}
 extern "C" void tables(int *vx, int *vy, int *opp)
 {
     for (int j = 0; j < Q; ++j) { vx[j] = cvx(j); vy[j] = cvy(j); opp[j] = copp(j); }
@@ -69,6 +76,7 @@ def lib(tmp_path_factory):
     L.forward_moments.argtypes = [dp, dp]
     L.inverse_populations.argtypes = [dp, C.c_int, dp]
     L.wall_moments.argtypes = [dp, dp]
+    L.wall_tables.argtypes = [ip, ip]
     return L
 
 
@@ -119,3 +127,18 @@ def test_wall_state_moments_are_the_rho_and_E_rows(lib):
         out = np.zeros(2)
         lib.wall_moments(np.ascontiguousarray(row), out)
         assert np.allclose(out, M[:2] @ row, rtol=0, atol=1e-12)
+
+
+def test_each_side_lists_the_links_that_enter_across_it(lib):
+    """A wall's corrections are kept per entering link (Sec. 7): west, east,
+    south, north each list exactly the four velocities that point into the
+    lattice across that side, and the slot lookup inverts the list."""
+    link, slot = np.zeros(16, dtype=np.int32), np.zeros(4 * Q, dtype=np.int32)
+    lib.wall_tables(link, slot)
+    v = _golden_velocities()
+    inward = [v[:, 0] > 0, v[:, 0] < 0, v[:, 1] > 0, v[:, 1] < 0]  # west, east, south, north
+    for side in range(4):
+        assert sorted(link[4 * side:4 * side + 4]) == sorted(np.flatnonzero(inward[side]))
+        for j in range(Q):
+            want = list(link[4 * side:4 * side + 4]).index(j) if inward[side][j] else -1
+            assert slot[Q * side + j] == want
