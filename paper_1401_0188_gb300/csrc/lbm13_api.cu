@@ -12,6 +12,7 @@
 
 #include "../../include/lbm13.h"
 #include "lbm13_internal.h"
+#include "lbm13_coef.h"
 #include "lbm13_tma.h"
 #include "lbm13_pair.h"
 
@@ -211,57 +212,7 @@ int derive(const lbm13_params &p, double *out)
 template <typename C>
 void fill_coef(lbm13_t h, Coef<C> &k)
 {
-    const double *D = h->derived;
-    const lbm13_params &p = h->p;
-    k.E0 = C(p.E0);
-    k.cer = C(D[6]);
-    k.ceE = C(p.c_epsE);
-    k.cwr = C(p.c_vpi_rho);
-    k.cwE = C(p.c_vpi_E);
-    k.h1 = C(D[2]);
-    k.k1 = C(D[3]);
-    k.Q10 = C(p.c1 + D[2] + D[3] * p.E0);
-    k.h2 = C(D[4]);
-    k.k2 = C(p.k2);
-    k.R10 = C(D[5] + D[4] + p.k2 * p.E0);
-    const double *s = D + 9;
-    k.l_eps = C(s[2] / kD[2]);
-    k.l_vpi = C(s[3] / kD[3]);
-    k.l_q = C(s[6] / kD[6]);
-    k.l_r = C(s[8] / kD[8]);
-    k.l_XX = C(s[10] / kD[10]);
-    k.l_XY = C(s[11] / kD[11]);
-    k.l_XXe = C(s[12] / kD[12]);
-    k.gx = C(h->b.gx);
-    k.gy = C(h->b.gy);
-    k.rho_ref = C(h->b.rho_ref);
-    // Energy source q (Sec. 9): equilibria at E + 13 q, so q_eq and r_eq
-    // shift by 13 q k1 and 13 q k2 per unit of j.
-    const double q = h->b.heat;
-    k.Qh = q == 0.0 ? k.Q10 : C(p.c1 + D[2] + D[3] * (p.E0 + 13.0 * q));
-    k.Rh = q == 0.0 ? k.R10 : C(D[5] + D[4] + p.k2 * (p.E0 + 13.0 * q));
-    // Scalar block: values of the E, eps, varpi polynomials on the shells
-    // (rest, unit axes, diagonals, distance-2 axes); the increment of a
-    // population of shell s is eps_s d_eps + varpi_s d_varpi with
-    // d_eps = l_eps (c_erho rho + c_epsE E - eps), all linear in the shell sums.
-    const double ME[4] = {-28, -15, -2, 24}, Meps[4] = {140, -2, -67, 34}, Mvpi[4] = {-12, 8, -6, 1};
-    const double le = s[2] / kD[2], lv = s[3] / kD[3];
-    for (int sh = 0; sh < 4; ++sh)
-        for (int l = 0; l < 4; ++l)
-            k.B[sh][l] = C(Meps[sh] * le * (D[6] + p.c_epsE * ME[l] - Meps[l]) +
-                           Mvpi[sh] * lv * (p.c_vpi_rho + p.c_vpi_E * ME[l] - Mvpi[l]));
-    // Source: E* gains 26 q, eps and varpi relax toward equilibria raised by
-    // 13 q c_epsE and 13 q c_varpiE.
-    for (int sh = 0; sh < 4; ++sh)
-        k.src[sh] = C(q == 0.0 ? 0.0
-                               : ME[sh] * 26.0 * q / kD[1] + Meps[sh] * le * p.c_epsE * 13.0 * q +
-                                     Mvpi[sh] * lv * p.c_vpi_E * 13.0 * q);
-    // Tensor block: XX = X1 + 4 X9, XXe = -4 X1 + X9 relaxed and mapped back.
-    const double lXX = s[10] / kD[10], lXXe = s[12] / kD[12];
-    k.t1X1 = C(-lXX - 16.0 * lXXe);
-    k.t1X9 = C(-4.0 * lXX + 4.0 * lXXe);
-    k.t9X1 = C(-4.0 * lXX + 4.0 * lXXe);
-    k.t9X9 = C(-16.0 * lXX - lXXe);
+    collision_coef(h->p, h->derived, h->b, k);
 }
 
 // Coefficients (a0 .. a4) of P(drho, dE) = a0 + a1 drho + a2 dE + a3 drho^2 +

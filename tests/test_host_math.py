@@ -1,11 +1,13 @@
-"""The kernels' per-node basis code on the host, without a GPU: the velocity
-tables and the factorised moment transforms of csrc/lbm13_math.cuh (host and
-device functions, which the library's host code also uses) are compiled with
-the host compiler and checked against the paper's velocity set
-(tests/golden/velocities.txt, Sec. 1 and Sec. 2) and the oracle's dense moment
-matrix M of Eq. (d2q13-polynomes) and its inverse M^T D^-1.
+"""The kernels' per-node code on the host, without a GPU: the velocity and
+wall-link tables, the factorised moment transforms and the collision of
+csrc/lbm13_math.cuh (host and device functions, which the library's host code
+also uses), with the collision constants lbm13_create computes
+(csrc/lbm13_coef.h), are compiled with the host compiler and checked against
+the paper's velocity set (tests/golden/velocities.txt, Sec. 1 and Sec. 2), the
+oracle's dense moment matrix M of Eq. (d2q13-polynomes) and its inverse
+M^T D^-1, and the oracle's collision.
 
-This checks the source of the transforms the step kernels run (pair sums and
+This checks the source of the arithmetic the step kernels run (pair sums and
 differences instead of 2 x 169 products); the GPU parity tests check the
 compiled kernels end to end."""
 import ctypes as C
@@ -26,7 +28,26 @@ FIELDS = ("rho", "E", "eps", "vpi", "jx", "jy", "qx", "qy", "rx", "ry", "XX", "X
 
 SRC = r"""
 #include "lbm13_internal.h"
+#include "lbm13_coef.h"
 using namespace lbm13;
+// one collision of the step kernels' code, on deviations df = f - w
+template <typename C>
+void collide_dev(const lbm13_params *p, const double *D, const lbm13_boundary *b, const double *df, double *out)
+{
+    Coef<C> k;
+    collision_coef(*p, D, *b, k);
+    C f[Q];
+    for (int j = 0; j < Q; ++j) f[j] = C(df[j]);
+    if (b->gx != 0.0 || b->gy != 0.0 || b->heat != 0.0) collide<true>(f, k);
+    else collide<false>(f, k);
+    for (int j = 0; j < Q; ++j) out[j] = double(f[j]);
+}
+extern "C" void host_collide(const lbm13_params *p, const double *D, const lbm13_boundary *b, const double *df,
+                             int fp32, double *out)
+{
+    if (fp32) collide_dev<float>(p, D, b, df, out);
+    else collide_dev<double>(p, D, b, df, out);
+}
 extern "C" void wall_tables(int *link, int *slot)
 {
     for (int s = 0; s < 4; ++s) {
@@ -77,6 +98,7 @@ def lib(tmp_path_factory):
     L.inverse_populations.argtypes = [dp, C.c_int, dp]
     L.wall_moments.argtypes = [dp, dp]
     L.wall_tables.argtypes = [ip, ip]
+    L.host_collide.argtypes = [C.c_void_p, dp, C.c_void_p, dp, C.c_int, dp]
     return L
 
 
@@ -142,3 +164,36 @@ def test_each_side_lists_the_links_that_enter_across_it(lib):
         for j in range(Q):
             want = list(link[4 * side:4 * side + 4]).index(j) if inward[side][j] else -1
             assert slot[Q * side + j] == want
+
+
+@pytest.mark.parametrize("case", ["plain", "force", "buoyancy_and_source"])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_kernel_collision_equals_the_oracle(lib, case, fp32):
+    """One collision (Sec. 2: moments, equilibria at j + F/2 and E + 13 q,
+    relaxation, force and source, back to populations) by the kernels' code,
+    with the constants lbm13_create computes (lbm13_derive, then the host's
+    collision constants), against the oracle's dense 13 x 13 collision, on
+    populations around equilibria of random (rho, u, T): FP64 to round-off
+    (measured 2e-16), FP32 deviation storage within 1e-8 (measured 1.6e-9)."""
+    from paper_1401_0188_gb300 import build, lbm13
+    build.build()
+    p = O.pstar(0.05, 0.71)
+    st, D = lbm13.lbm13_derive(p)
+    assert st == 0
+    bnd = {"plain": O.boundary(), "force": O.boundary(gx=3e-4, gy=-2e-4, rho_ref=0.0),
+           "buoyancy_and_source": O.boundary(gy=-1e-3, rho_ref=1.0, heat=2e-5)}[case]
+    lat = O.Lattice(2, 2, p, bnd)
+    w = lat.constants()["w"]
+    T0 = lat.constants()["T0"]
+    rng = np.random.default_rng(14)
+    P, B = lbm13.make_params(p), lbm13.make_boundary(bnd)
+    worst = 0.0
+    for _ in range(32):
+        one = O.Lattice(2, 2, p, bnd)
+        one.set_equilibrium(1 + 0.02 * rng.standard_normal(), 0.03 * rng.standard_normal(),
+                            0.03 * rng.standard_normal(), T0 + 0.01 * rng.standard_normal())
+        f = one.get_raw()[:, 0, 0] * (1 + 1e-2 * rng.standard_normal(Q))
+        out = np.zeros(Q)
+        lib.host_collide(C.addressof(P), np.ascontiguousarray(D), C.addressof(B), np.ascontiguousarray(f - w), fp32, out)
+        worst = max(worst, np.abs(out + w - lat.collide_node(f)).max())
+    assert worst < (1e-8 if fp32 else 1e-14), worst
