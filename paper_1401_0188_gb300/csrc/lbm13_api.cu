@@ -215,74 +215,10 @@ void fill_coef(lbm13_t h, Coef<C> &k)
     collision_coef(h->p, h->derived, h->b, k);
 }
 
-// Coefficients (a0 .. a4) of P(drho, dE) = a0 + a1 drho + a2 dE + a3 drho^2 +
-// a4 drho dE from values of P, which is exactly of that form: every
-// equilibrium moment at rho = 1 + drho, E = E0 + dE, j = rho u is a
-// combination of rho, E, rho^2 and rho E (Eq. d2q13-moments-equil).  The
-// sample points rho = 1, 1 +- 1/2 and E0, E0 +- 1/2 give the coefficients
-// without truncation error.
-template <typename F>
-void quadratic_coefficients(F P, double a[5])
-{
-    const double h = 0.5;
-    const double p00 = P(0.0, 0.0), pp0 = P(h, 0.0), pm0 = P(-h, 0.0);
-    const double p0p = P(0.0, h), p0m = P(0.0, -h), ppp = P(h, h);
-    a[0] = p00;
-    a[1] = (pp0 - pm0) / (2.0 * h);
-    a[2] = (p0p - p0m) / (2.0 * h);
-    a[3] = (pp0 + pm0 - 2.0 * p00) / (2.0 * h * h);
-    a[4] = (ppp - pp0 - p0p + p00) / (h * h);
-}
-
-// Deviation of the equilibrium populations for the wall state (drho, dE) and
-// wall velocity (ux, uy), from the double coefficients of the lattice.
-void wall_equilibrium(lbm13_t h, double drho, double dE, double ux, double uy, double f[Q])
-{
-    const double rho = 1.0 + drho;
-    equilibrium_dev(drho, dE, rho * ux, rho * uy, h->kd, f);
-}
-
 template <typename C>
 void fill_walls(lbm13_t h, WallArgs<C> *w)
 {
-    const lbm13_wall *src[4] = {&h->b.west, &h->b.east, &h->b.south, &h->b.north};
-    for (int s = 0; s < 4; ++s) {
-        const lbm13_wall &in = *src[s];
-        WallArgs<C> &o = w[s];
-        const double ux = s <= EAST ? 0.0 : in.u_t, uy = s <= EAST ? in.u_t : 0.0;
-        o.kind = in.kind;
-        o.needs_data = in.kind == WALL_MIXED || (in.kind == WALL_BB && in.u_t != 0.0);
-        o.ux = C(ux);
-        o.uy = C(uy);
-        o.base = C(26.0 * in.T - 28.0);
-        o.eT = C(26.0 * (in.T - (h->p.E0 + 28.0) / 26.0));
-        o.mass_flux = in.kind == WALL_MIXED && h->b.wall_density == LBM13_WALL_DENSITY_ZERO_FLUX;
-        o.wsum = C(h->derived[22 + 1] + 2.0 * h->derived[22 + 9]);
-        // zero-flux density: even parts of the unit-density wall equilibrium on
-        // the outgoing unit and distance-2 normal links
-        double e[Q];
-        wall_equilibrium(h, 0.0, 26.0 * (in.T - (h->p.E0 + 28.0) / 26.0) + 13.0 * (ux * ux + uy * uy), ux, uy, e);
-        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
-        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
-        o.zf_ea = C(0.5 * (e[ja] + e[copp(ja)]));
-        o.zf_eb = C(0.5 * (e[jb] + e[copp(jb)]));
-        for (int i = 0; i < 4; ++i) {
-            const int j = wall_link(s, i), jn = copp(j);
-            const bool normal = s <= EAST ? cvy(j) == 0 : cvx(j) == 0;
-            const bool abb = in.kind == WALL_MIXED && normal;
-            double a[5];
-            quadratic_coefficients(
-                [&](double dr, double de) {
-                    double f[Q];
-                    wall_equilibrium(h, dr, de, ux, uy, f);
-                    return abb ? f[j] + f[jn] : f[j] - f[jn];
-                },
-                a);
-            for (int m = 0; m < 5; ++m) o.poly[i][m] = C(a[m]);
-        }
-    }
-    // a corner diagonal crosses both walls and takes both walls' corrections
-    // for its link (their slots above), each at its own wall's state
+    wall_coef(h->p, h->derived, h->b, h->kd, w);
 }
 
 template <typename T>

@@ -1,11 +1,12 @@
-// lbm13_coef.h -- the per-lattice constants of the collision (Coef, in
-// lbm13_math.cuh) from the free parameters, the derived constants of Sec. 2
-// (lbm13_derive's output) and the boundary's force and energy source.  Host
+// lbm13_coef.h -- the per-lattice constants of the step: those of the
+// collision (Coef, in lbm13_math.cuh) from the free parameters, the derived
+// constants of Sec. 2 (lbm13_derive's output) and the boundary's force and
+// energy source, and the wall arguments of the four sides (WallArgs, in
+// lbm13_internal.h) with the correction polynomials of Sec. 7's walls.  Host
 // code, used by lbm13_create.
 #pragma once
 
-#include "../../include/lbm13.h"
-#include "lbm13_math.cuh"
+#include "lbm13_internal.h"
 
 namespace lbm13 {
 
@@ -63,6 +64,81 @@ void collision_coef(const lbm13_params &p, const double *D, const lbm13_boundary
     k.t1X9 = C(-4.0 * lXX + 4.0 * lXXe);
     k.t9X1 = C(-4.0 * lXX + 4.0 * lXXe);
     k.t9X9 = C(-16.0 * lXX - lXXe);
+}
+
+// Coefficients (a0 .. a4) of P(drho, dE) = a0 + a1 drho + a2 dE + a3 drho^2 +
+// a4 drho dE from values of P, which is exactly of that form: every
+// equilibrium moment at rho = 1 + drho, E = E0 + dE, j = rho u is a
+// combination of rho, E, rho^2 and rho E (Eq. d2q13-moments-equil).  The
+// sample points rho = 1, 1 +- 1/2 and E0, E0 +- 1/2 give the coefficients
+// without truncation error.
+template <typename F>
+void quadratic_coefficients(F P, double a[5])
+{
+    const double h = 0.5;
+    const double p00 = P(0.0, 0.0), pp0 = P(h, 0.0), pm0 = P(-h, 0.0);
+    const double p0p = P(0.0, h), p0m = P(0.0, -h), ppp = P(h, h);
+    a[0] = p00;
+    a[1] = (pp0 - pm0) / (2.0 * h);
+    a[2] = (p0p - p0m) / (2.0 * h);
+    a[3] = (pp0 + pm0 - 2.0 * p00) / (2.0 * h * h);
+    a[4] = (ppp - pp0 - p0p + p00) / (h * h);
+}
+
+// Deviation of the equilibrium populations for the wall state (drho, dE) and
+// wall velocity (ux, uy), from the double collision constants kd.
+inline void wall_equilibrium(const Coef<double> &kd, double drho, double dE, double ux, double uy, double f[Q])
+{
+    const double rho = 1.0 + drho;
+    equilibrium_dev(drho, dE, rho * ux, rho * uy, kd, f);
+}
+
+// The four sides' wall arguments (west, east, south, north): kinds, wall
+// velocity and temperature terms, zero-flux constants and the correction
+// polynomial of each entering link.  D: lbm13_derive's constants; kd: the
+// double collision constants of the same lattice.
+template <typename C>
+void wall_coef(const lbm13_params &p, const double *D, const lbm13_boundary &b, const Coef<double> &kd,
+               WallArgs<C> *w)
+{
+    const lbm13_wall *src[4] = {&b.west, &b.east, &b.south, &b.north};
+    for (int s = 0; s < 4; ++s) {
+        const lbm13_wall &in = *src[s];
+        WallArgs<C> &o = w[s];
+        const double ux = s <= EAST ? 0.0 : in.u_t, uy = s <= EAST ? in.u_t : 0.0;
+        o.kind = in.kind;
+        o.needs_data = in.kind == WALL_MIXED || (in.kind == WALL_BB && in.u_t != 0.0);
+        o.ux = C(ux);
+        o.uy = C(uy);
+        o.base = C(26.0 * in.T - 28.0);
+        o.eT = C(26.0 * (in.T - (p.E0 + 28.0) / 26.0));
+        o.mass_flux = in.kind == WALL_MIXED && b.wall_density == LBM13_WALL_DENSITY_ZERO_FLUX;
+        o.wsum = C(D[22 + 1] + 2.0 * D[22 + 9]);
+        // zero-flux density: even parts of the unit-density wall equilibrium on
+        // the outgoing unit and distance-2 normal links
+        double e[Q];
+        wall_equilibrium(kd, 0.0, 26.0 * (in.T - (p.E0 + 28.0) / 26.0) + 13.0 * (ux * ux + uy * uy), ux, uy, e);
+        const int ja = s == WEST ? 3 : s == EAST ? 1 : s == SOUTH ? 4 : 2;
+        const int jb = s == WEST ? 11 : s == EAST ? 9 : s == SOUTH ? 12 : 10;
+        o.zf_ea = C(0.5 * (e[ja] + e[copp(ja)]));
+        o.zf_eb = C(0.5 * (e[jb] + e[copp(jb)]));
+        for (int i = 0; i < 4; ++i) {
+            const int j = wall_link(s, i), jn = copp(j);
+            const bool normal = s <= EAST ? cvy(j) == 0 : cvx(j) == 0;
+            const bool abb = in.kind == WALL_MIXED && normal;
+            double a[5];
+            quadratic_coefficients(
+                [&](double dr, double de) {
+                    double f[Q];
+                    wall_equilibrium(kd, dr, de, ux, uy, f);
+                    return abb ? f[j] + f[jn] : f[j] - f[jn];
+                },
+                a);
+            for (int m = 0; m < 5; ++m) o.poly[i][m] = C(a[m]);
+        }
+    }
+    // a corner diagonal crosses both walls and takes both walls' corrections
+    // for its link (their slots above), each at its own wall's state
 }
 
 } // namespace lbm13

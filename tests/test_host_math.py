@@ -42,6 +42,16 @@ void collide_dev(const lbm13_params *p, const double *D, const lbm13_boundary *b
     else collide<false>(f, k);
     for (int j = 0; j < Q; ++j) out[j] = double(f[j]);
 }
+extern "C" void host_wall_polys(const lbm13_params *p, const double *D, const lbm13_boundary *b, double *poly)
+{
+    Coef<double> kd;
+    collision_coef(*p, D, *b, kd);
+    WallArgs<double> w[4];
+    wall_coef(*p, D, *b, kd, w);
+    for (int s = 0; s < 4; ++s)
+        for (int i = 0; i < 4; ++i)
+            for (int m = 0; m < 5; ++m) poly[(s * 4 + i) * 5 + m] = w[s].poly[i][m];
+}
 extern "C" void host_collide(const lbm13_params *p, const double *D, const lbm13_boundary *b, const double *df,
                              int fp32, double *out)
 {
@@ -99,6 +109,7 @@ def lib(tmp_path_factory):
     L.wall_moments.argtypes = [dp, dp]
     L.wall_tables.argtypes = [ip, ip]
     L.host_collide.argtypes = [C.c_void_p, dp, C.c_void_p, dp, C.c_int, dp]
+    L.host_wall_polys.argtypes = [C.c_void_p, dp, C.c_void_p, dp]
     return L
 
 
@@ -197,3 +208,52 @@ def test_kernel_collision_equals_the_oracle(lib, case, fp32):
         lib.host_collide(C.addressof(P), np.ascontiguousarray(D), C.addressof(B), np.ascontiguousarray(f - w), fp32, out)
         worst = max(worst, np.abs(out + w - lat.collide_node(f)).max())
     assert worst < (1e-8 if fp32 else 1e-14), worst
+
+
+def test_wall_corrections_are_the_oracle_equilibrium_parts(lib):
+    """Sec. 7's walls, as the kernels apply them: each entering link gains a
+    correction that is a quadratic polynomial in the wall state's deviations
+    (drho_w, dE_w), fitted on the host (csrc/lbm13_coef.h).  At any wall state
+    it must equal the oracle's equilibrium at that state: the odd part
+    f_eq,j - f_eq,-j on bounce-back links (R14) and the even part
+    f_eq,j + f_eq,-j on the normal links of a temperature wall (R11, anti-
+    bounce-back), as deviations from the rest populations, with the wall's
+    own velocity (R12's density and the temperature wall's energy enter only
+    through that state)."""
+    from paper_1401_0188_gb300 import build, lbm13
+    build.build()
+    p = O.pstar(0.05, 0.71)
+    st, D = lbm13.lbm13_derive(p)
+    assert st == 0
+    T0 = (p["E0"] + 28.0) / 26.0
+    B, M = O.WALL_BB, O.WALL_MIXED
+    bnd = O.boundary(west=O.wall(M, 0.02, T0 + 0.01), east=O.wall(B, -0.03), south=O.wall(M, -0.01, T0 - 0.01),
+                     north=O.wall(B, 0.025))
+    poly = np.zeros(80)
+    Pp, Bb = lbm13.make_params(p), lbm13.make_boundary(bnd)
+    lib.host_wall_polys(C.addressof(Pp), np.ascontiguousarray(D), C.addressof(Bb), poly)
+    poly = poly.reshape(4, 4, 5)
+    link, slot = np.zeros(16, dtype=np.int32), np.zeros(4 * Q, dtype=np.int32)
+    lib.wall_tables(link, slot)
+    vx, vy = O.velocities()
+    opp = [int(np.flatnonzero((vx == -vx[j]) & (vy == -vy[j]))[0]) for j in range(Q)]
+    eq = O.Lattice(2, 2, p)
+    w = eq.constants()["w"]
+    rng = np.random.default_rng(15)
+    sides = [bnd["west"], bnd["east"], bnd["south"], bnd["north"]]
+    for s, side in enumerate(sides):
+        u = (0.0, side["u_t"]) if s < 2 else (side["u_t"], 0.0)
+        for _ in range(6):
+            rho_w = 1 + 0.05 * rng.standard_normal()
+            T_w = T0 + 0.02 * rng.standard_normal()
+            eq.set_equilibrium(rho_w, u[0], u[1], T_w)
+            feq = eq.get_raw()[:, 0, 0] - w
+            dE = rho_w * (26 * T_w - 28) + 13 * rho_w * (u[0] ** 2 + u[1] ** 2) - p["E0"]
+            for i in range(4):
+                j = link[4 * s + i]
+                normal = vy[j] == 0 if s < 2 else vx[j] == 0
+                want = feq[j] + feq[opp[j]] if (side["kind"] == M and normal) else feq[j] - feq[opp[j]]
+                a = poly[s, i]
+                x, y = rho_w - 1, dE
+                got = a[0] + x * (a[1] + x * a[3] + y * a[4]) + y * a[2]
+                assert got == pytest.approx(want, abs=1e-14), (s, j)
