@@ -1,15 +1,17 @@
 """The source of the step kernels' per-node code, checked on the host against
 the oracle without a GPU.
 
-The kernels resolve every link of a node next to an edge with one function
-(gather_body in csrc/lbm13_stepdev.cuh: periodic wrap, bounce-back and
-anti-bounce-back walls, the distance-2 links, corners), then collide and
-store (csrc/lbm13_math.cuh).  Those functions are plain C++ apart from their
-CUDA qualifiers, so this test compiles them with the host compiler (the
-qualifiers ignored, a scalar load for the device load, the one warp vote
-stubbed), sets up the lattice constants with the same host code lbm13_create
-uses (csrc/lbm13_coef.h), applies the three functions to every node for a
-number of steps and compares the populations with the oracle's.
+A step kernel thread runs process_column (csrc/lbm13_stepdev.cuh) on one to
+four rows of a column: the 13 pulls, the links that cross an x edge
+(periodic wrap or the wall rules of cross_wall), or, on the two bottom and
+two top rows, every link through gather_body (periodic wrap, bounce-back and
+anti-bounce-back walls, the distance-2 links, corners), then collide and store
+(csrc/lbm13_math.cuh).  Those functions are plain C++ apart from their CUDA
+qualifiers, so this test compiles them with the host compiler (the
+qualifiers ignored, a scalar load for the device load, the warp vote taken
+over one lane), sets up the lattice constants with the same host code
+lbm13_create uses (csrc/lbm13_coef.h), steps whole lattices with them and
+compares the populations with the oracle's.
 
 This is a check of the kernel source's logic, not a way to run the library:
 the library has no CPU path and refuses to run without CUDA.  The GPU parity
@@ -49,21 +51,33 @@ static inline bool __all_sync(unsigned, bool b) { return b; }
 #include "lbm13_stepdev.cuh"
 using namespace lbm13;
 
+// mode 0: every node through gather_body, collide and store; mode R > 0:
+// columns of R rows through process_column, the step kernels' per-thread
+// code (the warp vote over one lane: each column picks its own path)
 template <typename T, bool Force>
-static void sweep(const StepArgs<T, T> &a)
+static void sweep(const StepArgs<T, T> &a, int mode)
 {
-    for (int y = 0; y < a.ny; ++y)
+    T slot[Q];
+    if (mode == 0) {
+        for (int y = 0; y < a.ny; ++y)
+            for (int x = 0; x < a.nx; ++x) {
+                T f[Q];
+                gather_body(a, x, y, f, GlobalSrc<T, T>());
+                collide<Force>(f, a.k);
+                store(a, x, y, f);
+            }
+        return;
+    }
+    for (int y0 = 0; y0 < a.ny; y0 += mode)
         for (int x = 0; x < a.nx; ++x) {
-            T f[Q];
-            gather_body(a, x, y, f, GlobalSrc<T, T>());
-            collide<Force>(f, a.k);
-            store(a, x, y, f);
+            if (mode == 1) process_column<T, T, Force, 1>(a, x, y0, slot);
+            else process_column<T, T, Force, 2>(a, x, y0, slot);
         }
 }
 
 template <typename T>
 static void run(const lbm13_params &p, const double *D, const lbm13_boundary &b, int nx, int ny, int steps,
-                const double *f0, double *f1)
+                int mode, const double *f0, double *f1)
 {
     Coef<double> kd;
     collision_coef(p, D, b, kd);
@@ -93,8 +107,8 @@ static void run(const lbm13_params &p, const double *D, const lbm13_boundary &b,
         a.plane = plane;
         a.k = k;
         for (int i = 0; i < 4; ++i) a.wall[i] = w[i];
-        if (force) sweep<T, true>(a);
-        else sweep<T, false>(a);
+        if (force) sweep<T, true>(a, mode);
+        else sweep<T, false>(a, mode);
         cur ^= 1;
     }
     for (int j = 0; j < Q; ++j)
@@ -103,10 +117,10 @@ static void run(const lbm13_params &p, const double *D, const lbm13_boundary &b,
 }
 
 extern "C" void host_steps(const lbm13_params *p, const double *D, const lbm13_boundary *b, int nx, int ny,
-                           int fp32, int steps, const double *f0, double *f1)
+                           int fp32, int steps, int mode, const double *f0, double *f1)
 {
-    if (fp32) run<float>(*p, D, *b, nx, ny, steps, f0, f1);
-    else run<double>(*p, D, *b, nx, ny, steps, f0, f1);
+    if (fp32) run<float>(*p, D, *b, nx, ny, steps, mode, f0, f1);
+    else run<double>(*p, D, *b, nx, ny, steps, mode, f0, f1);
 }
 """
 
@@ -122,7 +136,7 @@ def lib(tmp_path_factory):
                            str(src), "-o", str(so)])
     L = C.CDLL(str(so))
     dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
-    L.host_steps.argtypes = [C.c_void_p, dp, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
+    L.host_steps.argtypes = [C.c_void_p, dp, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
     return L
 
 
@@ -147,12 +161,14 @@ def _cases(T0):
     }
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("fp32", [0, 1])
 @pytest.mark.parametrize("case", list(_cases(0.576)))
-def test_kernel_step_source_matches_the_oracle(lib, case, fp32):
-    """100 steps from perturbed populations: FP64 within 1e-12 of the oracle
-    (round-off of the different operation order), FP32 deviation storage
-    within 1e-7."""
+def test_kernel_step_source_matches_the_oracle(lib, case, fp32, mode):
+    """100 steps from perturbed populations, every node through the edge
+    gather (mode 0) or through the per-thread column code with one or two
+    rows per thread (modes 1, 2): FP64 within 1e-12 of the oracle (round-off
+    of the different operation order), FP32 deviation storage within 1e-7."""
     from paper_1401_0188_gb300 import build, lbm13
     build.build()
     p = O.pstar(0.05, 0.71)
@@ -166,7 +182,7 @@ def test_kernel_step_source_matches_the_oracle(lib, case, fp32):
     steps = 100
     f1 = np.zeros_like(f0)
     Pp, Bb = lbm13.make_params(p), lbm13.make_boundary(bnd)
-    lib.host_steps(C.addressof(Pp), np.ascontiguousarray(D), C.addressof(Bb), nx, ny, fp32, steps,
+    lib.host_steps(C.addressof(Pp), np.ascontiguousarray(D), C.addressof(Bb), nx, ny, fp32, steps, mode,
                    np.ascontiguousarray(f0), f1)
     o.step(steps)
     d = np.abs(f1 - o.get_raw()).max()
